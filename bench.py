@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Throughput of the incremental octree LOD update on one GB300 per rank.
+
+One step = one pass of the whole update path over the workload: reset the
+octree, then insert every batch of the stream (count, split, voxel claim,
+chunk allocation, scatter) with the batches already resident in HBM. The
+default workload is the 50M-point aerial scan in 1M-point batches.
+
+Prints one JSON line (rank 0). With --impl reference the CPU oracle is timed
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+REPO = os.path.dirname(os.path.abspath(__file__))
+if REPO not in sys.path:
+    sys.path.insert(0, REPO)
+
+METRIC = "Mpts/s inserted into octree (frac. of HBM roofline); p50/p99 batch latency vs plain"
+UNIT = "Mpts/s"
+L2_BYTES = 129 << 20
+CTL_BYTES = 192  # the library's control block, read once per expansion round
+
+# Algorithmic bytes each kernel is charged with (the per-update total is
+# 16 B + 20 B per batch point, 40 B per re-inserted point, 16 B per new voxel
+# and one zeroed grid per split):
+#   count1: reads every batch point once (16 B)
+#   spill:  reads every re-inserted point once (20 B with its gidx) and zeroes
+#           the new grids
+#   store:  writes every point with its gidx (20 B, batch and re-inserted) and
+#           every new voxel (16 B)
+#   advance, decide, merge_pending, end: no algorithmic bytes (re-traversal,
+#           bookkeeping)
+
+
+def kernel_alg_bytes(name: str, B: int, S: int, V: int, K: int, grid_bytes: int) -> int:
+    if name == "count1":
+        return 16 * B
+    if name == "spill":
+        return 20 * S + grid_bytes * K
+    if name == "store":
+        return 20 * (B + S) + 16 * V
+    return 0
+
+
+def update_alg_bytes(B, S, V, K, grid_bytes):
+    return 16 * B + 20 * B + 40 * S + 16 * V + grid_bytes * K
+
+
+def load_peaks():
+    path = os.path.join(REPO, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def make_workload(name: str, points: int | None):
+    from paper_2310_03567_gb300 import synth
+    if name == "aerial":
+        return synth.aerial_workload(n=points or 50_000_000), 22
+    if name == "uniform":
+        return synth.uniform_workload(n=points or 1_000_000), 20
+    if name == "clustered":
+        return synth.clustered_workload(n=points or 300_000_000), 21
+    if name == "mixed":
+        return synth.mixed_workload(n=points or 100_000_000), 22
+    raise ValueError(name)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(workload, budget_s: float = 12.0):
+    """The incremental oracle on the host, one core, on the first batches of the
+    workload until the time budget is used (at least one batch)."""
+    import oracle
+    w, root_log2 = workload
+    cfg = oracle.Config.make(root_min=w.root_min, root_log2=root_log2)
+    inc = oracle.Incremental(cfg)
+    pts = 0
+    t0 = time.perf_counter()
+    nb = 0
+    for b in w.batches():
+        rc = inc.insert(b)
+        if rc != oracle.OK:
+            raise RuntimeError(f"oracle insert failed: {rc}")
+        pts += len(b)
+        nb += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    inc.close()
+    return {"value": pts / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {nb} batches ({pts} points) of {w.name}, sequential incremental "
+                      f"oracle, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    workload = make_workload(args.workload, args.points)
+    w, root_log2 = workload
+    import oracle
+    cfg = oracle.Config.make(root_min=w.root_min, root_log2=root_log2)
+    nb = max(1, min(len(w.counts), args.ref_batches))
+    sample = list(w.batches())[:nb]
+    pts = sum(len(b) for b in sample)
+
+    def step():
+        inc = oracle.Incremental(cfg)
+        for b in sample:
+            assert inc.insert(b) == oracle.OK
+        inc.close()
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = pts * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": w.name, "batches_per_step": nb, "points_per_step": pts},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"first {nb} batches ({pts} points) of {w.name}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def percentile(v, q):
+    if not v:
+        return None
+    s = sorted(v)
+    k = min(len(s) - 1, max(0, int(round(q / 100.0 * (len(s) - 1)))))
+    return s[k]
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2310_03567_gb300 import simlod
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    simlod.load()
+
+    # each rank builds its own octree from its own stream (independent units)
+    w, root_log2 = make_workload(args.workload, args.points)
+    if rank:
+        from paper_2310_03567_gb300 import synth
+        if args.workload == "aerial":
+            w.points = synth.terrain(1 + 1000 * rank, w.n_points)
+    n_points = w.n_points
+    dev_pts = simlod.points_tensor(w.points)
+    batches = [(dev_pts.data_ptr() + int(o) * 16, int(c)) for o, c in zip(w.offsets, w.counts)]
+    max_batch = int(w.counts.max())
+    cfg = simlod.default_config(root_min=w.root_min, root_log2=root_log2,
+                                max_batch_points=max_batch,
+                                spill_capacity=max(8 << 20, 2 * max_batch),
+                                max_nodes=1 << 21)
+    data_bytes = max(4 << 30, n_points * 80)
+    arena = simlod.make_arena(cfg, data_bytes)
+    stream = torch.cuda.Stream()
+    tree = simlod.Octree(cfg, arena, stream=stream)
+
+    def step(lat=None):
+        tree.reset()
+        for ptr, cnt in batches:
+            if lat is not None:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            rc = tree.insert_ptr(ptr, cnt)
+            if rc != simlod.OK:
+                raise simlod.SimlodError(rc, "insert")
+            if lat is not None:
+                b.record(stream)
+                lat.append((a, b))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stats = tree.stats()  # counts of one full pass (the last warm-up step)
+
+    lat_events = []
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    tree.set_timing(True, clear=True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(lat_events)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    tree.set_timing(False)
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    ktime = tree.timing()
+    lat_ms = [a.elapsed_time(b) for a, b in lat_events]
+
+    # ---- end to end through the public API: host batches, H2D inside
+    host_pts = torch.from_numpy(np.ascontiguousarray(w.points).view(np.uint8).reshape(-1, 16))
+    host_pts = host_pts.pin_memory()
+    hptr = host_pts.data_ptr()
+    lib = simlod.load()
+
+    def e2e_step():
+        tree.reset()
+        for o, c in zip(w.offsets, w.counts):
+            rc = lib.simlod_insert_batch_host(tree.handle, hptr + int(o) * 16, int(c),
+                                              stream.cuda_stream)
+            if rc != simlod.OK:
+                raise simlod.SimlodError(rc, "insert_host")
+        return tree.stats()  # device-to-host read of the result
+
+    e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    del host_pts
+
+    # ---- roofline of the dominant kernel
+    peak, peak_src = load_peaks()
+    B, S, V, K = n_points, stats["spilled"], stats["voxels"], stats["splits"]
+    grid_bytes = (1 << (3 * cfg.grid_log2)) // 8
+    dom = max(ktime.items(), key=lambda kv: kv[1][1])
+    dom_name, (dom_launches, dom_ms) = dom
+    launches_per_step = dom_launches / args.steps
+    alg_per_step = kernel_alg_bytes(dom_name, B, S, V, K, grid_bytes)
+    avg_ms = dom_ms / max(dom_launches, 1)
+    achieved = (alg_per_step / max(launches_per_step, 1)) / (avg_ms * 1e-3) / 1e9 if avg_ms else 0.0
+    gpu_launches = sum(v[0] for v in ktime.values())
+    ms_per_step = ms_total / args.steps
+    value = n_points * world * args.steps / (ms_total * 1e-3) / 1e6
+    upd_bytes = update_alg_bytes(B, S, V, K, grid_bytes)
+    roofline_mpts = B / (upd_bytes / (peak * 1e9)) / 1e6
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": w.name, "batch_points": max_batch, "batches_per_step": len(batches),
+                   "points_per_step": n_points, "leaf_capacity": cfg.leaf_capacity,
+                   "chunk_points": cfg.chunk_points, "grid": 1 << cfg.grid_log2,
+                   "path": "plain per-kernel", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (%.0f MB of points)" % (n_points * 16 / 2**20)},
+        "latency_ms": {"p50": percentile(lat_ms, 50), "p99": percentile(lat_ms, 99),
+                       "batches": len(lat_ms)},
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": peak_src},
+        "update_roofline": {"alg_bytes_per_step": upd_bytes,
+                            "alg_bytes_per_point": upd_bytes / B,
+                            "achieved_gbs": upd_bytes / (ms_per_step * 1e-3) / 1e9,
+                            "roofline_mpts": roofline_mpts,
+                            "frac": value / world / roofline_mpts},
+        "update_counts": {"B": B, "S": S, "V": V, "K": K},
+        "kernels_ms_per_step": {k: v[1] / args.steps for k, v in ktime.items() if v[0]},
+        "gpu_launches": gpu_launches,
+        "e2e": {"value": n_points * world / e2e_s / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": n_points * 16,
+                "d2h_bytes_per_step": CTL_BYTES * (stats["rounds"] + 1)},
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline((w, root_log2), args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tree.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="aerial",
+                    choices=["aerial", "uniform", "clustered", "mixed"])
+    ap.add_argument("--points", type=int, default=None)
+    ap.add_argument("--ref-batches", type=int, default=2)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

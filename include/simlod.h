@@ -1,0 +1,224 @@
+/*
+ * simlod.h: C ABI of the GB300 incremental octree LOD update.
+ *
+ * The method is SimLOD's per-batch update (Schuetz, Herzberger, Wimmer,
+ * "SimLOD: Simultaneous LOD Generation and Rendering", Section 5): every
+ * arriving batch of points is counted into the current leaves, leaves holding
+ * more than T points split into 8 children until no leaf spills (Section 5.1),
+ * every point samples a voxel in the 128^3 occupancy grid of each inner node
+ * on its way down (Section 5.2), chunks are allocated from a pool and a bump
+ * allocator (Sections 3.2, 3.4, 5.3) and points and voxels are stored into
+ * linked chunks of C records (Section 5.4).
+ *
+ * Determinism: the result after every batch is a pure function of the point
+ * stream. Where the GPU would race, the contract fixes the winner: a voxel
+ * takes the colour of the point with the lowest global arrival index (gidx)
+ * among the points that reach its empty cell, per node (Section 5.2's "first
+ * point"). Orders inside chunks, chunk addresses and pool order are not part
+ * of the result; the canonical snapshot sorts them away.
+ *
+ * Memory: the caller owns one device buffer, the arena, the analogue of the
+ * paper's persistent buffer (Section 3.2). The library carves its node table,
+ * work buffers and the bump-allocated data region (grids and chunks) out of it
+ * and never allocates device memory itself. Host-side state (the handle, a
+ * small pinned control-block mirror, CUDA events) is the library's.
+ *
+ * Errors: every entry point returns an int status, 0 on success and a
+ * negative SIMLOD_ERR_* code otherwise. Nothing throws across the ABI and no
+ * kernel traps. A device-side capacity failure (arena, nodes, spill, backlog)
+ * poisons the handle: later calls return SIMLOD_ERR_POISONED (the sticky
+ * cause is in simlod_stats.sticky_status) and simlod_destroy still works.
+ *
+ * Threading: a handle is not thread-safe; calls on one handle must be
+ * serialised by the caller. Different handles are independent.
+ */
+#ifndef SIMLOD_H
+#define SIMLOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SIMLOD_API __attribute__((visibility("default")))
+#else
+#define SIMLOD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A point: int32 coordinates (1 mm units in the workloads here) and RGBA8,
+ * 16 bytes, 16-byte aligned in device buffers. The paper's SIM format stores
+ * float xyz + RGBA8 in the same 16 bytes (Section 7.1). */
+typedef struct {
+  int32_t x, y, z;
+  uint8_t r, g, b, a;
+} simlod_point;
+
+/* Octree parameters. simlod_config_default() fills the paper's values. */
+typedef struct {
+  int32_t root_min[3];       /* root cube [root_min, root_min + 2^root_log2) per axis */
+  uint32_t root_log2;        /* 1..31 */
+  uint32_t leaf_capacity;    /* T: a leaf splits when it would hold more (50,000; Section 3.1) */
+  uint32_t chunk_points;     /* C: records per chunk (1,000; Section 3.4), 1..65,536 */
+  uint32_t grid_log2;        /* G: sampling grid 2^G per axis (7 = 128^3; Section 3.3), 1..7 */
+  uint32_t max_expand_iters; /* expansion rounds per update; 0 = root_log2 + 1 (enough) */
+  uint64_t max_batch_points; /* largest n accepted by one insert */
+  uint64_t spill_capacity;   /* points re-inserted from split leaves, per update */
+  uint64_t backlog_capacity; /* new voxels per update (10M suggested; Section 5.2) */
+  uint64_t max_nodes;        /* node table size */
+  uint32_t flags;            /* reserved, 0 */
+  uint32_t reserved;
+} simlod_config;
+
+/* Canonical snapshot records (see simlod_snapshot). rgba = r | g<<8 | b<<16 | a<<24. */
+typedef struct {
+  uint32_t level, is_inner;
+  int32_t min[3];
+  uint32_t log2size;
+  uint64_t n_points, n_voxels, n_chunks;
+} simlod_node_rec;
+
+typedef struct {
+  int32_t x, y, z;
+  uint32_t rgba;
+  uint32_t gidx;
+} simlod_point_rec;
+
+typedef struct {
+  uint32_t cell; /* cx + 2^G (cy + 2^G cz) */
+  int32_t x, y, z;
+  uint32_t rgba;
+} simlod_voxel_rec;
+
+/* Snapshot buffers: caller-owned host arrays and their capacities (in
+ * records). Call once with all three pointers NULL to learn the sizes, then
+ * again with buffers at least that large. */
+typedef struct {
+  simlod_node_rec* nodes;
+  uint64_t nodes_capacity;
+  simlod_point_rec* points;
+  uint64_t points_capacity;
+  simlod_voxel_rec* voxels;
+  uint64_t voxels_capacity;
+  uint64_t n_nodes, n_points, n_voxels; /* out */
+} simlod_snapshot_t;
+
+typedef struct {
+  uint64_t batches, points, rejected_batches;
+  uint64_t spilled, splits, voxels, iterations_max;
+  uint64_t rounds; /* expansion rounds summed over updates (one control-block read each) */
+  uint64_t nodes;
+  uint64_t chunks_bumped, chunks_pool;
+  uint64_t arena_bytes, data_bytes, data_used;
+  /* the last applied update */
+  uint64_t last_points, last_spilled, last_splits, last_voxels, last_iterations;
+  int32_t sticky_status; /* the error that poisoned the handle, or 0 */
+  uint32_t device_error_bits;
+} simlod_stats;
+
+/* Per-kernel device time, accumulated while timing is enabled. */
+#define SIMLOD_N_KERNELS 8
+typedef struct {
+  const char* name[SIMLOD_N_KERNELS];
+  uint64_t launches[SIMLOD_N_KERNELS];
+  double ms[SIMLOD_N_KERNELS];
+} simlod_timing;
+
+enum {
+  SIMLOD_OK = 0,
+  SIMLOD_ERR_INVALID_ARG = -1,
+  SIMLOD_ERR_OUT_OF_BOUNDS = -2, /* a point outside the root cube: batch rejected, no change */
+  SIMLOD_ERR_ARENA_FULL = -3,    /* data region exhausted (grids + chunks) */
+  SIMLOD_ERR_BACKLOG_FULL = -4,  /* more new voxels in one update than backlog_capacity */
+  SIMLOD_ERR_SPILL_FULL = -5,    /* more re-inserted points than spill_capacity */
+  SIMLOD_ERR_ITER_CAP = -6,      /* expansion needed more than max_expand_iters rounds */
+  SIMLOD_ERR_TIMEOUT = -7,       /* a bounded device wait gave up */
+  SIMLOD_ERR_POISONED = -8,      /* an earlier device error: only destroy/stats/status work */
+  SIMLOD_ERR_CUDA = -9,          /* a CUDA runtime call failed */
+  SIMLOD_ERR_NODES_FULL = -10,   /* node table exhausted */
+  SIMLOD_ERR_TOO_MANY_POINTS = -11 /* 2^32 points per octree (gidx is 32-bit) */
+};
+
+/* Fill cfg with the paper's parameters: T = 50,000, C = 1,000, 128^3 grids,
+ * a 10M-voxel backlog; root cube [0, 2^20)^3; batches up to 16M points. */
+SIMLOD_API void simlod_config_default(simlod_config* cfg);
+
+/* Bytes of arena needed for cfg with a data region of data_bytes (grids and
+ * chunks). Returns SIMLOD_ERR_INVALID_ARG for an invalid cfg. */
+SIMLOD_API int simlod_arena_bytes(const simlod_config* cfg, uint64_t data_bytes,
+                                  uint64_t* arena_bytes);
+
+typedef struct simlod simlod_t; /* opaque handle */
+
+/* Create an octree in the caller's device arena (256-byte aligned,
+ * arena_bytes long; it must stay allocated until simlod_destroy). Everything
+ * left after the fixed regions becomes the data region. The arena is
+ * initialised on `stream` (a cudaStream_t; NULL = the legacy default stream)
+ * and the call returns after that work completed. The octree starts as one
+ * empty leaf, the root. */
+SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t arena_bytes,
+                             void* stream, simlod_t** out);
+
+/* Insert one batch of n points (Section 5): d_pts is a device pointer to n
+ * 16-byte records (16-byte aligned) that stay unchanged until the call
+ * returns. The batch is one complete update: expansion, voxel sampling,
+ * chunk allocation and storing. Batches are applied in call order; the k-th
+ * point ever accepted gets gidx k. n = 0 is a no-op.
+ *
+ * The work runs on `stream`. The call returns when the update is complete on
+ * the device (the expansion rounds are steered from the host, one
+ * device-to-host read of the control block per round). Returns
+ * SIMLOD_ERR_OUT_OF_BOUNDS, with the octree and the gidx counter unchanged,
+ * when any point lies outside the root cube. */
+SIMLOD_API int simlod_insert_batch(simlod_t* h, const simlod_point* d_pts, uint64_t n,
+                                   void* stream);
+
+/* As simlod_insert_batch for a batch in host memory: the points are copied
+ * into a staging region of the arena on `stream` first (page-locked host
+ * memory makes the copy asynchronous and fast). */
+SIMLOD_API int simlod_insert_batch_host(simlod_t* h, const simlod_point* h_pts, uint64_t n,
+                                        void* stream);
+
+/* Frame-budget update (Section 7.2): apply batches 0, 1, ... in order, and
+ * before starting batch k > 0 check the time spent since the call began; once
+ * it exceeds budget_ns, stop. Batches are never cut. *consumed receives the
+ * number of batches applied; the caller passes the rest in the next frame.
+ * d_batches[k] are device pointers as in simlod_insert_batch. */
+SIMLOD_API int simlod_frame_update(simlod_t* h, const simlod_point* const* d_batches,
+                                   const uint64_t* counts, uint32_t n_batches,
+                                   uint64_t budget_ns, void* stream, uint32_t* consumed);
+
+/* Empty the octree (one empty root leaf, gidx counter 0) without touching
+ * the arena allocation; the handle's poison is cleared. */
+SIMLOD_API int simlod_reset(simlod_t* h, void* stream);
+
+/* Wait for the handle's last stream and report a device error, if any. */
+SIMLOD_API int simlod_sync(simlod_t* h);
+
+/* Counters since create/reset (synchronises). */
+SIMLOD_API int simlod_get_stats(simlod_t* h, simlod_stats* out);
+
+/* Canonical export (synchronises; doubles as a checkpoint). Nodes are sorted
+ * by (level, ix, iy, iz) with ix = (min_x - root_min_x) >> log2size; each
+ * leaf's points follow in node order sorted by gidx; each inner node's voxels
+ * follow in node order sorted by cell. n_chunks is the length of the node's
+ * chunk list, ceil(count / C) (Section 5.3). */
+SIMLOD_API int simlod_snapshot(simlod_t* h, simlod_snapshot_t* snap);
+
+/* Record CUDA events around every kernel launch (on the launching stream)
+ * and accumulate per-kernel device time; enable = 0 stops, clear resets. */
+SIMLOD_API int simlod_set_timing(simlod_t* h, int enable, int clear);
+SIMLOD_API int simlod_get_timing(simlod_t* h, simlod_timing* out);
+
+/* Release host-side state. The arena is the caller's and is not touched. */
+SIMLOD_API int simlod_destroy(simlod_t* h);
+
+/* Static text for a status code. */
+SIMLOD_API const char* simlod_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

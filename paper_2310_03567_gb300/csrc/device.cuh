@@ -1,0 +1,574 @@
+// Device-side data layout and the phase functions of one octree update.
+//
+// The update of one batch follows Section 5 of the paper, re-planned for a
+// GPU that can hold the whole per-update working set in L2:
+//
+//  count1  every batch point walks from the root to its leaf. At every inner
+//          node on the way it tests the node's occupancy bit (Section 3.3);
+//          an empty cell makes the point a contender for a new voxel. At the
+//          leaf it takes a ticket from the leaf's counter (Section 5.1,
+//          "Counting"); the ticket is its final slot if the leaf does not
+//          split. The leaf and ticket are kept per point (the cursor).
+//  decide  per candidate node: a leaf whose stored + counted points exceed T
+//          splits (Section 5.1, "Splitting"): 8 children, a zeroed grid, its
+//          points reserved in the spill buffer. Any other counted node is
+//          final and gets its chunks now (Section 5.3).
+//  spill   per split leaf: copy its stored points (with gidx) to the spill
+//          buffer, zero its grid, free its chunks (Section 3.4).
+//  advance points whose cursor leaf split (batch or spill) sample that
+//          node's fresh grid and move one level down, counting into the
+//          child. Repeated with decide/spill until nothing splits: the
+//          paper's iterative deepening, but each round touches only the
+//          points that have to move.
+//  store   every point goes to its cursor leaf at its ticket slot; every new
+//          voxel goes to its node (Section 5.4); occupancy bits are set here,
+//          after all claims of the update were made.
+//
+// Voxel claims: the paper lets the first point that finds an empty cell win.
+// Here all contenders of an update for a (node, cell) meet in an open-
+// addressing table with a 64-bit atomicMin on (gidx << 32 | rgba), so the
+// lowest arrival index wins regardless of thread timing. The table entries of
+// an update are listed (the backlog of Section 5.2) and cleared by store.
+#pragma once
+
+#include <cstdint>
+
+#include "simlod.h"
+
+namespace sl {
+
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr unsigned long long HASH_EMPTY = ~0ull;
+constexpr uint32_t FULL_MASK = 0xFFFFFFFFu;
+constexpr int MAX_PROBES = 1 << 14;
+constexpr uint32_t REF_BYTES = 256;  // chunk and grid references count 256-byte units
+constexpr uint32_t CHUNK_HEADER = 16;
+
+// Sticky device error bits.
+enum : uint32_t {
+  E_ARENA = 1u,
+  E_NODES = 2u,
+  E_SPILL = 4u,
+  E_BACKLOG = 8u,
+  E_ALLOC_REFS = 16u,
+  E_INTERNAL = 32u,
+  E_POOL = 64u,
+};
+
+// Control block at the start of the arena.
+struct Ctl {
+  unsigned long long base;           // gidx of the next accepted point
+  unsigned long long bump;           // bytes taken from the data region
+  unsigned long long chunks_bumped;  // chunks taken from the data region
+  unsigned int n_nodes;
+  int pool_top;                      // chunk refs in the pool
+  unsigned int error;                // sticky E_* bits
+  unsigned int reject;               // out-of-cube point seen in this update
+  unsigned int spill_count;          // spill entries of this update
+  unsigned int nkeys;                // new voxels (backlog entries) of this update
+  unsigned int alloc_seq;            // alloc_refs entries of this update
+  unsigned int split_count;          // split-list entries of this update
+  unsigned int pending_free;         // freed chunk refs waiting for the pool
+  unsigned int pad0;
+  unsigned long long st_batches, st_points, st_rejected, st_spilled, st_splits, st_voxels,
+      st_iter_max, st_rounds;
+  unsigned long long last_points, last_spilled, last_splits, last_voxels, last_iters;
+  unsigned long long pad1[3];
+};
+static_assert(sizeof(Ctl) % 16 == 0, "Ctl size");
+
+// Per-node metadata that the count/advance hot loops do not touch.
+struct NodeMeta {
+  int32_t min[3];
+  uint32_t level;
+  uint32_t n_chunks;
+  uint32_t head, tail;  // chunk list (points of a leaf, voxels of an inner node)
+  uint32_t grid;        // occupancy grid ref, NONE for leaves
+  uint32_t st_nch;      // store map of the current update: chunks before allocation,
+  uint32_t st_tail;     //   the tail before allocation,
+  uint32_t st_seq;      //   first alloc_refs entry of the newly allocated chunks
+  uint32_t pad[5];
+};
+static_assert(sizeof(NodeMeta) == 64, "NodeMeta size");
+
+struct HSlot {
+  unsigned long long key;  // (node << 3G) | cell, HASH_EMPTY when free
+  unsigned long long val;  // (gidx << 32) | rgba of the best contender so far
+};
+
+struct SplitEntry {
+  uint32_t node;
+  uint32_t spill_off;
+};
+
+// Everything a phase needs: arena pointers and the configuration.
+struct Ctx {
+  Ctl* ctl;
+  uint32_t* child;  // first child id or NONE (leaf), per node
+  uint32_t* cnt;    // per-update counter: new points (leaf) or new voxels (inner)
+  uint32_t* num;    // stored points (leaf) or voxels (inner)
+  NodeMeta* meta;
+  uint32_t* pool;
+  uint32_t* pending;
+  uint32_t* alloc_refs;
+  SplitEntry* splits;
+  int4* sp_pt;
+  uint32_t* sp_gidx;
+  uint32_t* sp_cur;
+  uint32_t* sp_slot;
+  uint32_t* b_cur;
+  uint32_t* b_slot;
+  HSlot* hash;
+  uint2* keys;  // backlog: (hash slot, voxel slot)
+  uint8_t* data;
+  unsigned long long data_bytes;
+  int4* staging;
+  int32_t rmin[3];
+  uint32_t rlog2, T, C, G;
+  uint32_t chunk_bytes, chunk_units, grid_bytes;
+  uint32_t hash_mask;
+  uint32_t max_nodes, max_chunks, spill_cap, backlog_cap, max_splits;
+  uint64_t max_batch;
+};
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned long long fmix64(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+__device__ __forceinline__ void set_error(const Ctx& c, uint32_t bits) {
+  atomicOr(&c.ctl->error, bits);
+}
+
+__device__ __forceinline__ uint8_t* chunk_ptr(const Ctx& c, uint32_t ref) {
+  return c.data + (size_t)ref * REF_BYTES;
+}
+
+__device__ __forceinline__ uint32_t* chunk_next(const Ctx& c, uint32_t ref) {
+  return reinterpret_cast<uint32_t*>(chunk_ptr(c, ref));
+}
+
+__device__ __forceinline__ int4* chunk_recs(const Ctx& c, uint32_t ref) {
+  return reinterpret_cast<int4*>(chunk_ptr(c, ref) + CHUNK_HEADER);
+}
+
+__device__ __forceinline__ uint32_t* chunk_aux(const Ctx& c, uint32_t ref) {
+  return reinterpret_cast<uint32_t*>(chunk_ptr(c, ref) + CHUNK_HEADER + 16u * c.C);
+}
+
+// A reference that stays inside the data region for `bytes` bytes.
+__device__ __forceinline__ bool ref_ok(const Ctx& c, uint32_t ref, uint32_t bytes) {
+  return ref != NONE && (unsigned long long)ref * REF_BYTES + bytes <= c.data_bytes;
+}
+
+__device__ __forceinline__ uint32_t* grid_words(const Ctx& c, uint32_t ref) {
+  return reinterpret_cast<uint32_t*>(c.data + (size_t)ref * REF_BYTES);
+}
+
+// Coordinates relative to the root minimum; false when outside the root cube.
+__device__ __forceinline__ bool rel_coords(const Ctx& c, int4 p, uint32_t& rx, uint32_t& ry,
+                                           uint32_t& rz) {
+  long long dx = (long long)p.x - c.rmin[0];
+  long long dy = (long long)p.y - c.rmin[1];
+  long long dz = (long long)p.z - c.rmin[2];
+  long long side = 1ll << c.rlog2;
+  rx = (uint32_t)dx;
+  ry = (uint32_t)dy;
+  rz = (uint32_t)dz;
+  return dx >= 0 && dy >= 0 && dz >= 0 && dx < side && dy < side && dz < side;
+}
+
+// Octant of a point inside a node of side 2^L (L >= 1): bit L-1 per axis.
+__device__ __forceinline__ uint32_t octant(uint32_t rx, uint32_t ry, uint32_t rz, uint32_t L) {
+  uint32_t s = L - 1u;
+  return ((rx >> s) & 1u) | (((ry >> s) & 1u) << 1) | (((rz >> s) & 1u) << 2);
+}
+
+// Cell of a point in the 2^G grid of a node of side 2^L: per axis
+// ((p - min) << G) >> L, where p - min is the low L bits of the root-relative
+// coordinate (Section 3.3).
+__device__ __forceinline__ uint32_t cell_axis(uint32_t r, uint32_t L, uint32_t G) {
+  uint32_t local = (L >= 32u) ? r : (r & ((1u << L) - 1u));
+  return (L >= G) ? (local >> (L - G)) : (local << (G - L));
+}
+
+__device__ __forceinline__ uint32_t cell_index(uint32_t rx, uint32_t ry, uint32_t rz, uint32_t L,
+                                               uint32_t G) {
+  return cell_axis(rx, L, G) | (cell_axis(ry, L, G) << G) | (cell_axis(rz, L, G) << (2u * G));
+}
+
+// -------------------------------------------------------- voxel claims
+
+// A new (node, cell) key was installed at table slot h: list it in the
+// backlog and give it a voxel slot of its node.
+__device__ __forceinline__ void new_voxel(const Ctx& c, uint32_t h, uint32_t node) {
+  uint32_t e = atomicAdd(&c.ctl->nkeys, 1u);
+  if (e >= c.backlog_cap) {
+    set_error(c, E_BACKLOG);
+    return;
+  }
+  uint32_t t = atomicAdd(&c.cnt[node], 1u);
+  c.keys[e] = make_uint2(h, c.num[node] + t);
+}
+
+// Offer (gidx, rgba) as the colour of cell `key`; the lowest gidx wins.
+__device__ __forceinline__ void hash_claim(const Ctx& c, unsigned long long key,
+                                           unsigned long long val, uint32_t node) {
+  uint32_t h = (uint32_t)fmix64(key) & c.hash_mask;
+  for (int probe = 0; probe < MAX_PROBES; ++probe) {
+    HSlot* s = c.hash + h;
+    unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&s->key);
+    if (k == HASH_EMPTY) {
+      unsigned long long old = atomicCAS(&s->key, HASH_EMPTY, key);
+      if (old == HASH_EMPTY) {
+        atomicMin(&s->val, val);
+        new_voxel(c, h, node);
+        return;
+      }
+      k = old;
+    }
+    if (k == key) {
+      atomicMin(&s->val, val);
+      return;
+    }
+    h = (h + 1u) & c.hash_mask;
+  }
+  set_error(c, E_BACKLOG);
+}
+
+// All 32 lanes call. Lanes with `want` contend for (node, cell) = key; lanes
+// with equal keys are merged first and only the lowest gidx goes to the table.
+__device__ __forceinline__ void warp_claim(const Ctx& c, bool want, unsigned long long key,
+                                           uint32_t gidx, uint32_t rgba, uint32_t node) {
+  unsigned m = __ballot_sync(FULL_MASK, want);
+  if (!want) return;
+  unsigned grp = __match_any_sync(m, key);
+  unsigned best = __reduce_min_sync(grp, gidx);
+  if (gidx == best) hash_claim(c, key, ((unsigned long long)gidx << 32) | rgba, node);
+}
+
+// All 32 lanes call. Lanes with `valid` count one point into `leaf` and get
+// their slot there: stored points + their rank among this update's points.
+__device__ __forceinline__ uint32_t warp_count(const Ctx& c, bool valid, uint32_t leaf) {
+  const uint32_t lane = lane_id();
+  unsigned m = __ballot_sync(FULL_MASK, valid);
+  uint32_t base = 0, rank = 0;
+  int leader = 0;
+  if (valid) {
+    unsigned grp = __match_any_sync(m, leaf);
+    leader = __ffs(grp) - 1;
+    rank = __popc(grp & ((1u << lane) - 1u));
+    if ((int)lane == leader) base = c.num[leaf] + atomicAdd(&c.cnt[leaf], (uint32_t)__popc(grp));
+  }
+  base = __shfl_sync(FULL_MASK, base, leader);
+  return base + rank;
+}
+
+// ------------------------------------------------------------ phase: count1
+
+// Iteration 1 for the batch points [0, n): descend, claim, count.
+__device__ void phase_count1(const Ctx& c, const int4* pts, uint64_t n, unsigned long long base,
+                             uint64_t warp0, uint64_t nwarps) {
+  const uint32_t lane = lane_id();
+  for (uint64_t w = warp0; w * 32 < n; w += nwarps) {
+    uint64_t i = w * 32 + lane;
+    bool valid = i < n;
+    int4 p = valid ? __ldg(pts + i) : make_int4(0, 0, 0, 0);
+    uint32_t rx = 0, ry = 0, rz = 0;
+    if (valid && !rel_coords(c, p, rx, ry, rz)) {
+      atomicOr(&c.ctl->reject, 1u);
+      valid = false;
+    }
+    const uint32_t gidx = (uint32_t)(base + i);
+    uint32_t node = 0, L = c.rlog2;
+    bool walking = valid;
+    while (__any_sync(FULL_MASK, walking)) {
+      bool inner = false, want = false;
+      uint32_t cell = 0, nxt = 0;
+      if (walking) {
+        uint32_t ch = c.child[node];
+        if (ch == NONE) {
+          walking = false;
+        } else {
+          inner = true;
+          cell = cell_index(rx, ry, rz, L, c.G);
+          uint32_t word = grid_words(c, c.meta[node].grid)[cell >> 5];
+          want = ((word >> (cell & 31u)) & 1u) == 0u;
+          nxt = ch + octant(rx, ry, rz, L);
+        }
+      }
+      warp_claim(c, want, ((unsigned long long)node << (3u * c.G)) | cell, gidx, (uint32_t)p.w,
+                 node);
+      if (inner) {
+        node = nxt;
+        --L;
+      }
+    }
+    uint32_t slot = warp_count(c, valid, node);
+    if (valid) {
+      c.b_cur[i] = node;
+      c.b_slot[i] = slot;
+    }
+  }
+}
+
+// ----------------------------------------------------------- phase: advance
+
+// Later iterations: items whose cursor node split in the previous round
+// sample that node's fresh grid and count into the child below.
+__device__ __forceinline__ void advance_item(const Ctx& c, bool valid, int4 p, uint32_t gidx,
+                                             uint32_t* cur, uint32_t* slot_out) {
+  uint32_t node = valid ? *cur : 0;
+  uint32_t ch = valid ? c.child[node] : NONE;
+  bool moving = valid && ch != NONE;
+  uint32_t rx = 0, ry = 0, rz = 0, L = 0, cell = 0, nxt = 0;
+  if (moving) {
+    rel_coords(c, p, rx, ry, rz);
+    L = c.rlog2 - c.meta[node].level;
+    cell = cell_index(rx, ry, rz, L, c.G);
+    nxt = ch + octant(rx, ry, rz, L);
+  }
+  // the grid of a node split in this update is empty until store
+  warp_claim(c, moving, ((unsigned long long)node << (3u * c.G)) | cell, gidx, (uint32_t)p.w,
+             node);
+  uint32_t s = warp_count(c, moving, nxt);
+  if (moving) {
+    *cur = nxt;
+    *slot_out = s;
+  }
+}
+
+__device__ void phase_advance(const Ctx& c, const int4* pts, uint64_t n, unsigned long long base,
+                              uint32_t n_spill, uint64_t warp0, uint64_t nwarps) {
+  const uint32_t lane = lane_id();
+  const uint64_t wb = (n + 31) / 32, ws = (n_spill + 31ull) / 32;
+  for (uint64_t w = warp0; w < wb + ws; w += nwarps) {
+    if (w < wb) {
+      uint64_t i = w * 32 + lane;
+      bool valid = i < n;
+      int4 p = valid ? __ldg(pts + i) : make_int4(0, 0, 0, 0);
+      uint32_t dummy_cur = 0, dummy_slot = 0;
+      advance_item(c, valid, p, (uint32_t)(base + i), valid ? c.b_cur + i : &dummy_cur,
+                   valid ? c.b_slot + i : &dummy_slot);
+    } else {
+      uint64_t e = (w - wb) * 32 + lane;
+      bool valid = e < n_spill;
+      int4 p = valid ? c.sp_pt[e] : make_int4(0, 0, 0, 0);
+      uint32_t g = valid ? c.sp_gidx[e] : 0u;
+      uint32_t dummy_cur = 0, dummy_slot = 0;
+      advance_item(c, valid, p, g, valid ? c.sp_cur + e : &dummy_cur,
+                   valid ? c.sp_slot + e : &dummy_slot);
+    }
+  }
+}
+
+// ------------------------------------------------------------ phase: decide
+
+// Take up to k refs from the pool; returns how many and the first index.
+__device__ __forceinline__ uint32_t pool_take(const Ctx& c, uint32_t k, int* first) {
+  int t = *reinterpret_cast<volatile int*>(&c.ctl->pool_top);
+  for (int it = 0; it < (1 << 20) && t > 0; ++it) {
+    int take = t < (int)k ? t : (int)k;
+    int old = atomicCAS(&c.ctl->pool_top, t, t - take);
+    if (old == t) {
+      *first = t - take;
+      return (uint32_t)take;
+    }
+    t = old;
+  }
+  if (t > 0) set_error(c, E_POOL);
+  return 0;
+}
+
+// Section 5.3: give node `id` ceil(total / C) chunks, pool first, then the
+// bump allocator; link them and record the store map for this update.
+__device__ void alloc_chunks(const Ctx& c, uint32_t id, uint32_t total) {
+  NodeMeta& m = c.meta[id];
+  const uint32_t have = m.n_chunks;
+  const uint32_t need = (uint32_t)(((unsigned long long)total + c.C - 1) / c.C);
+  m.st_nch = have;
+  m.st_tail = m.tail;
+  m.st_seq = 0;
+  if (need <= have) return;
+  const uint32_t k = need - have;
+  const uint32_t seq = atomicAdd(&c.ctl->alloc_seq, k);
+  if ((unsigned long long)seq + k > c.max_chunks) {
+    set_error(c, E_ALLOC_REFS);
+    return;
+  }
+  m.st_seq = seq;
+  int pfirst = 0;
+  const uint32_t from_pool = pool_take(c, k, &pfirst);
+  const uint32_t rest = k - from_pool;
+  unsigned long long off = 0;
+  if (rest) {
+    off = atomicAdd(&c.ctl->bump, (unsigned long long)rest * c.chunk_bytes);
+    if (off + (unsigned long long)rest * c.chunk_bytes > c.data_bytes) {
+      set_error(c, E_ARENA);
+      return;
+    }
+    atomicAdd(&c.ctl->chunks_bumped, (unsigned long long)rest);
+  }
+  uint32_t prev = m.tail;
+  for (uint32_t q = 0; q < k; ++q) {
+    uint32_t ref = q < from_pool ? c.pool[pfirst + (int)q]
+                                 : (uint32_t)(off / REF_BYTES) + (q - from_pool) * c.chunk_units;
+    c.alloc_refs[seq + q] = ref;
+    *chunk_next(c, ref) = NONE;
+    if (prev == NONE) m.head = ref;
+    else *chunk_next(c, prev) = ref;
+    prev = ref;
+  }
+  m.tail = prev;
+  m.n_chunks = need;
+}
+
+// Section 5.1: split leaf `id` whose count exceeds T.
+__device__ void split_leaf(const Ctx& c, uint32_t id) {
+  const uint32_t c0 = atomicAdd(&c.ctl->n_nodes, 8u);
+  if ((unsigned long long)c0 + 8 > c.max_nodes) {
+    set_error(c, E_NODES);
+    return;
+  }
+  NodeMeta& m = c.meta[id];
+  const uint32_t Lc = c.rlog2 - m.level - 1u;  // children's log2 size
+  for (uint32_t k = 0; k < 8; ++k) {
+    NodeMeta cm;
+    cm.min[0] = m.min[0] + (int32_t)((k & 1u) << Lc);
+    cm.min[1] = m.min[1] + (int32_t)(((k >> 1) & 1u) << Lc);
+    cm.min[2] = m.min[2] + (int32_t)(((k >> 2) & 1u) << Lc);
+    cm.level = m.level + 1u;
+    cm.n_chunks = 0;
+    cm.head = cm.tail = NONE;
+    cm.grid = NONE;
+    cm.st_nch = 0;
+    cm.st_tail = NONE;
+    cm.st_seq = 0;
+    for (int q = 0; q < 5; ++q) cm.pad[q] = 0;
+    c.meta[c0 + k] = cm;
+    c.child[c0 + k] = NONE;
+    c.cnt[c0 + k] = 0;
+    c.num[c0 + k] = 0;
+  }
+  const unsigned long long g = atomicAdd(&c.ctl->bump, (unsigned long long)c.grid_bytes);
+  if (g + c.grid_bytes > c.data_bytes) {
+    set_error(c, E_ARENA);
+    return;
+  }
+  m.grid = (uint32_t)(g / REF_BYTES);
+  const uint32_t stored = c.num[id];
+  const uint32_t s0 = atomicAdd(&c.ctl->spill_count, stored);
+  if ((unsigned long long)s0 + stored > c.spill_cap) {
+    set_error(c, E_SPILL);
+    return;
+  }
+  const uint32_t e = atomicAdd(&c.ctl->split_count, 1u);
+  if (e >= c.max_splits) {
+    set_error(c, E_NODES);
+    return;
+  }
+  c.splits[e] = SplitEntry{id, s0};
+  c.cnt[id] = 0;
+  c.child[id] = c0;
+}
+
+__device__ __forceinline__ void decide_node(const Ctx& c, uint32_t id) {
+  const uint32_t k = c.cnt[id];
+  if (k == 0) return;
+  if (c.child[id] == NONE) {
+    const uint32_t total = c.num[id] + k;
+    const uint32_t L = c.rlog2 - c.meta[id].level;
+    if (total > c.T && L > 0) {
+      split_leaf(c, id);
+      return;
+    }
+    alloc_chunks(c, id, total);
+    c.num[id] = total;
+  } else {
+    alloc_chunks(c, id, c.num[id] + k);
+    c.num[id] += k;
+  }
+  c.cnt[id] = 0;
+}
+
+// Candidates: the nodes split in the previous round (their voxels are now
+// all claimed) and the node id range [n_lo, n_hi). If the batch was rejected
+// (a point outside the root cube), undo the counters and claims instead.
+__device__ void phase_decide(const Ctx& c, uint32_t s_lo, uint32_t s_hi, uint32_t n_lo,
+                             uint32_t n_hi, uint64_t t0, uint64_t nthreads) {
+  const bool rejected = *reinterpret_cast<volatile unsigned int*>(&c.ctl->reject) != 0u;
+  const uint64_t ns = s_hi - s_lo, nn = n_hi - n_lo;
+  if (rejected) {
+    for (uint64_t t = t0; t < nn; t += nthreads) c.cnt[n_lo + t] = 0;
+    const uint32_t nk = *reinterpret_cast<volatile unsigned int*>(&c.ctl->nkeys);
+    for (uint64_t t = t0; t < nk && t < c.backlog_cap; t += nthreads) {
+      HSlot* s = c.hash + c.keys[t].x;
+      s->key = HASH_EMPTY;
+      s->val = HASH_EMPTY;
+    }
+    return;
+  }
+  for (uint64_t t = t0; t < ns + nn; t += nthreads) {
+    uint32_t id = t < ns ? c.splits[s_lo + t].node : (uint32_t)(n_lo + (t - ns));
+    decide_node(c, id);
+  }
+}
+
+// -------------------------------------------------------------- phase: store
+
+__device__ __forceinline__ void store_rec(const Ctx& c, uint32_t node, uint32_t slot, int4 rec,
+                                          uint32_t aux) {
+  const NodeMeta& m = c.meta[node];
+  const uint32_t j = slot / c.C, q = slot - j * c.C;
+  uint32_t ref = NONE;
+  if (j + 1u == m.st_nch) {
+    ref = m.st_tail;
+  } else if (j >= m.st_nch) {
+    const unsigned long long at = (unsigned long long)m.st_seq + (j - m.st_nch);
+    if (at < c.max_chunks) ref = c.alloc_refs[at];
+  }
+  if (!ref_ok(c, ref, c.chunk_bytes)) {
+    set_error(c, E_INTERNAL);
+    return;
+  }
+  chunk_recs(c, ref)[q] = rec;
+  chunk_aux(c, ref)[q] = aux;
+}
+
+__device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned long long base,
+                            uint32_t n_spill, uint32_t n_keys, uint64_t t0, uint64_t nthreads) {
+  for (uint64_t i = t0; i < n; i += nthreads)
+    store_rec(c, c.b_cur[i], c.b_slot[i], __ldg(pts + i), (uint32_t)(base + i));
+  for (uint64_t e = t0; e < n_spill; e += nthreads)
+    store_rec(c, c.sp_cur[e], c.sp_slot[e], c.sp_pt[e], c.sp_gidx[e]);
+  const uint32_t G = c.G, cmask = (1u << (3u * G)) - 1u, amask = (1u << G) - 1u;
+  for (uint64_t e = t0; e < n_keys; e += nthreads) {
+    const uint2 k = c.keys[e];
+    HSlot* s = c.hash + k.x;
+    const unsigned long long key = s->key, val = s->val;
+    const uint32_t node = (uint32_t)(key >> (3u * G)), cell = (uint32_t)key & cmask;
+    const NodeMeta& m = c.meta[node];
+    const uint32_t L = c.rlog2 - m.level;
+    const uint32_t cx = cell & amask, cy = (cell >> G) & amask, cz = cell >> (2u * G);
+    // Section 3.4: the voxel is a point at the (floor of the) cell centre
+    int4 v;
+    v.x = m.min[0] + (int32_t)(((2ull * cx + 1ull) << L) >> (G + 1u));
+    v.y = m.min[1] + (int32_t)(((2ull * cy + 1ull) << L) >> (G + 1u));
+    v.z = m.min[2] + (int32_t)(((2ull * cz + 1ull) << L) >> (G + 1u));
+    v.w = (int32_t)(uint32_t)val;
+    store_rec(c, node, k.y, v, cell);
+    atomicOr(grid_words(c, m.grid) + (cell >> 5), 1u << (cell & 31u));
+    s->key = HASH_EMPTY;
+    s->val = HASH_EMPTY;
+  }
+}
+
+}  // namespace sl

@@ -1,0 +1,827 @@
+// Kernels and host API of the C ABI in include/simlod.h (plain form: one
+// kernel per phase, expansion rounds steered from the host).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "device.cuh"
+#include "simlod.h"
+
+using namespace sl;
+
+// ================================================================= kernels
+
+namespace {
+
+constexpr int BLOCK = 256;
+
+__global__ void k_init(Ctx c) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Ctl* t = c.ctl;
+    memset(t, 0, sizeof(Ctl));
+    t->n_nodes = 1;
+    NodeMeta m;
+    memset(&m, 0, sizeof(m));
+    m.min[0] = c.rmin[0];
+    m.min[1] = c.rmin[1];
+    m.min[2] = c.rmin[2];
+    m.level = 0;
+    m.head = m.tail = NONE;
+    m.grid = NONE;
+    m.st_tail = NONE;
+    c.meta[0] = m;
+    c.child[0] = NONE;
+    c.cnt[0] = 0;
+    c.num[0] = 0;
+  }
+}
+
+__global__ void k_fill_hash(HSlot* h, uint64_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    h[i].key = HASH_EMPTY;
+    h[i].val = HASH_EMPTY;
+  }
+}
+
+__global__ void __launch_bounds__(BLOCK) k_count1(Ctx c, const int4* pts, uint64_t n,
+                                                   unsigned long long base) {
+  const uint64_t warps_per_block = blockDim.x / 32;
+  phase_count1(c, pts, n, base, blockIdx.x * warps_per_block + threadIdx.x / 32,
+               (uint64_t)gridDim.x * warps_per_block);
+}
+
+__global__ void __launch_bounds__(BLOCK) k_decide(Ctx c, uint32_t s_lo, uint32_t s_hi,
+                                                   uint32_t n_lo, uint32_t n_hi) {
+  phase_decide(c, s_lo, s_hi, n_lo, n_hi, blockIdx.x * (uint64_t)blockDim.x + threadIdx.x,
+               (uint64_t)gridDim.x * blockDim.x);
+}
+
+// One block per split leaf: zero its new grid, copy its stored points and
+// their gidx into its spill range, hand its chunks to the pending-free list.
+__global__ void __launch_bounds__(BLOCK) k_spill(Ctx c, uint32_t s_lo, uint32_t s_hi) {
+  constexpr uint32_t ROUND = 1024;
+  __shared__ uint32_t refs[ROUND];
+  __shared__ uint32_t s_nch, s_free0, s_n, s_bad;
+  for (uint32_t e = s_lo + blockIdx.x; e < s_hi; e += gridDim.x) {
+    const SplitEntry se = c.splits[e];
+    const uint32_t id = se.node;
+    NodeMeta& m = c.meta[id];
+    int4* g = reinterpret_cast<int4*>(grid_words(c, m.grid));
+    for (uint32_t q = threadIdx.x; q < c.grid_bytes / 16u; q += blockDim.x)
+      g[q] = make_int4(0, 0, 0, 0);
+    if (threadIdx.x == 0) {
+      s_bad = 0;
+      s_nch = m.n_chunks;
+      s_n = c.num[id];
+      s_free0 = atomicAdd(&c.ctl->pending_free, m.n_chunks);
+      if ((unsigned long long)s_free0 + m.n_chunks > c.max_chunks) set_error(c, E_POOL);
+    }
+    __syncthreads();
+    const uint32_t nch = s_nch, n = s_n, free0 = s_free0;
+    const bool ok = (unsigned long long)free0 + nch <= c.max_chunks;
+    uint32_t walk = m.head;  // used by thread 0 only
+    for (uint32_t r0 = 0; r0 < nch; r0 += ROUND) {
+      const uint32_t cnt = min(ROUND, nch - r0);
+      if (threadIdx.x == 0) {
+        for (uint32_t q = 0; q < cnt; ++q) {
+          if (!ref_ok(c, walk, c.chunk_bytes)) {  // list shorter than n_chunks
+            set_error(c, E_INTERNAL);
+            s_bad = 1;
+            break;
+          }
+          refs[q] = walk;
+          walk = *chunk_next(c, walk);
+        }
+      }
+      __syncthreads();
+      if (s_bad) break;
+      const uint64_t lo = (uint64_t)r0 * c.C;
+      const uint64_t hi = min((uint64_t)n, (uint64_t)(r0 + cnt) * c.C);
+      for (uint64_t idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
+        const uint32_t j = (uint32_t)(idx / c.C), q = (uint32_t)(idx - (uint64_t)j * c.C);
+        const uint32_t ref = refs[j - r0];
+        const uint64_t dst = se.spill_off + idx;
+        c.sp_pt[dst] = chunk_recs(c, ref)[q];
+        c.sp_gidx[dst] = chunk_aux(c, ref)[q];
+        c.sp_cur[dst] = id;
+      }
+      if (ok)
+        for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) c.pending[free0 + r0 + q] = refs[q];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      m.n_chunks = 0;
+      m.head = m.tail = NONE;
+      c.num[id] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+// Move the chunks freed by this round's splits into the pool.
+__global__ void k_merge_pending(Ctx c) {
+  __shared__ int top;
+  __shared__ uint32_t np;
+  if (threadIdx.x == 0) {
+    top = c.ctl->pool_top;
+    np = c.ctl->pending_free;
+    if ((unsigned long long)top + np > c.max_chunks) {
+      set_error(c, E_POOL);
+      np = 0;
+    }
+  }
+  __syncthreads();
+  for (uint32_t q = threadIdx.x; q < np; q += blockDim.x) c.pool[top + q] = c.pending[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c.ctl->pool_top = top + (int)np;
+    c.ctl->pending_free = 0;
+  }
+}
+
+__global__ void __launch_bounds__(BLOCK) k_advance(Ctx c, const int4* pts, uint64_t n,
+                                                    unsigned long long base, uint32_t n_spill) {
+  const uint64_t warps_per_block = blockDim.x / 32;
+  phase_advance(c, pts, n, base, n_spill, blockIdx.x * warps_per_block + threadIdx.x / 32,
+                (uint64_t)gridDim.x * warps_per_block);
+}
+
+__global__ void __launch_bounds__(BLOCK) k_store(Ctx c, const int4* pts, uint64_t n,
+                                                  unsigned long long base, uint32_t n_spill,
+                                                  uint32_t n_keys) {
+  phase_store(c, pts, n, base, n_spill, n_keys, blockIdx.x * (uint64_t)blockDim.x + threadIdx.x,
+              (uint64_t)gridDim.x * blockDim.x);
+}
+
+// Close an applied update: advance gidx, fold the update into the stats and
+// clear the per-update counters.
+__global__ void k_end(Ctx c, uint64_t n, uint32_t iters) {
+  Ctl* t = c.ctl;
+  const unsigned long long nk = min((unsigned long long)t->nkeys, (unsigned long long)c.backlog_cap);
+  t->base += n;
+  t->st_batches += 1;
+  t->st_points += n;
+  t->st_spilled += t->spill_count;
+  t->st_splits += t->split_count;
+  t->st_voxels += nk;
+  if (iters > t->st_iter_max) t->st_iter_max = iters;
+  t->st_rounds += iters;
+  t->last_points = n;
+  t->last_spilled = t->spill_count;
+  t->last_splits = t->split_count;
+  t->last_voxels = nk;
+  t->last_iters = iters;
+  t->spill_count = 0;
+  t->nkeys = 0;
+  t->alloc_seq = 0;
+  t->split_count = 0;
+}
+
+// Close a rejected update (the decide kernel already undid its counters).
+__global__ void k_end_rejected(Ctx c) {
+  Ctl* t = c.ctl;
+  t->reject = 0;
+  t->nkeys = 0;
+  t->st_rejected += 1;
+}
+
+}  // namespace
+
+// ================================================================ host side
+
+enum KernelId { K_COUNT = 0, K_DECIDE, K_SPILL, K_MERGE, K_ADVANCE, K_STORE, K_END, K_OTHER };
+static const char* const kKernelNames[SIMLOD_N_KERNELS] = {
+    "count1", "decide", "spill", "merge_pending", "advance", "store", "end", "other"};
+
+struct Layout {
+  size_t ctl, child, cnt, num, meta, pool, pending, alloc_refs, splits, sp_pt, sp_gidx, sp_cur,
+      sp_slot, b_cur, b_slot, hash, keys, staging, data, end;
+  uint64_t hash_slots, max_chunks, max_splits, data_bytes;
+};
+
+struct simlod {
+  simlod_config cfg;
+  Ctx ctx;
+  Layout lay;
+  uint8_t* arena;
+  size_t arena_bytes;
+  Ctl* ctl_host;  // pinned mirror of the control block
+  unsigned long long base;  // host copy of the gidx counter
+  uint32_t n_nodes;         // host copy of the node count
+  int sticky;               // poison status
+  cudaStream_t last_stream;
+  int sm_count;
+  // timing
+  bool timing;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Pending {
+    int kernel;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  uint64_t launches[SIMLOD_N_KERNELS];
+  double ms[SIMLOD_N_KERNELS];
+};
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+uint64_t next_pow2(uint64_t v) {
+  uint64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+bool valid_config(const simlod_config* c) {
+  if (!c) return false;
+  if (c->root_log2 < 1 || c->root_log2 > 31) return false;
+  if (c->leaf_capacity < 1 || c->chunk_points < 1 || c->chunk_points > 65536) return false;
+  if (c->grid_log2 < 1 || c->grid_log2 > 7) return false;
+  if (c->max_batch_points < 1 || c->max_batch_points > (1ull << 32)) return false;
+  if (c->spill_capacity > 0xFFFFFFFFull || c->backlog_capacity < 1 ||
+      c->backlog_capacity > (1ull << 31))
+    return false;
+  if (c->max_nodes < 9 || c->max_nodes > (1ull << 31)) return false;
+  for (int a = 0; a < 3; ++a) {
+    long long hi = (long long)c->root_min[a] + (1ll << c->root_log2) - 1;
+    if (hi > 0x7FFFFFFFll) return false;
+  }
+  return true;
+}
+
+uint32_t chunk_bytes_of(const simlod_config* c) {
+  return (uint32_t)align_up(CHUNK_HEADER + 20ull * c->chunk_points, REF_BYTES);
+}
+
+uint32_t grid_bytes_of(const simlod_config* c) {
+  uint64_t bits = 1ull << (3 * c->grid_log2);
+  return (uint32_t)align_up(std::max<uint64_t>(bits / 8, 1), REF_BYTES);
+}
+
+// Place every region; the data region (grids and chunks) takes what is left
+// and pool / pending / alloc_refs hold one entry per chunk that fits in it.
+bool plan_layout(const simlod_config* c, size_t arena_bytes, Layout* L) {
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = align_up(o, 256);
+    o = at + bytes;
+    return at;
+  };
+  const uint64_t N = c->max_nodes, B = c->max_batch_points, S = c->spill_capacity;
+  L->max_splits = N / 8 + 1;
+  L->hash_slots = next_pow2(2 * c->backlog_capacity);
+  L->ctl = take(sizeof(Ctl));
+  L->child = take(4 * N);
+  L->cnt = take(4 * N);
+  L->num = take(4 * N);
+  L->meta = take(sizeof(NodeMeta) * N);
+  L->splits = take(sizeof(SplitEntry) * L->max_splits);
+  L->sp_pt = take(16 * S);
+  L->sp_gidx = take(4 * S);
+  L->sp_cur = take(4 * S);
+  L->sp_slot = take(4 * S);
+  L->b_cur = take(4 * B);
+  L->b_slot = take(4 * B);
+  L->hash = take(sizeof(HSlot) * L->hash_slots);
+  L->keys = take(sizeof(uint2) * c->backlog_capacity);
+  L->staging = take(16 * B);
+  const size_t fixed = align_up(o, 256);
+  if (arena_bytes < fixed) return false;
+  const uint64_t cb = chunk_bytes_of(c);
+  uint64_t max_chunks = (arena_bytes - fixed) / (cb + 12);
+  if (max_chunks > 0xFFFFFFF0ull) max_chunks = 0xFFFFFFF0ull;
+  L->max_chunks = max_chunks;
+  L->pool = take(4 * max_chunks);
+  L->pending = take(4 * max_chunks);
+  L->alloc_refs = take(4 * max_chunks);
+  L->data = align_up(o, 256);
+  if (arena_bytes < L->data) return false;
+  L->data_bytes = (arena_bytes - L->data) / REF_BYTES * REF_BYTES;
+  if (L->data_bytes / REF_BYTES > 0xFFFFFFFFull) L->data_bytes = 0xFFFFFFFFull * REF_BYTES;
+  L->end = L->data + L->data_bytes;
+  return true;
+}
+
+void make_ctx(simlod_t* h) {
+  Ctx& c = h->ctx;
+  const Layout& L = h->lay;
+  uint8_t* a = h->arena;
+  c.ctl = reinterpret_cast<Ctl*>(a + L.ctl);
+  c.child = reinterpret_cast<uint32_t*>(a + L.child);
+  c.cnt = reinterpret_cast<uint32_t*>(a + L.cnt);
+  c.num = reinterpret_cast<uint32_t*>(a + L.num);
+  c.meta = reinterpret_cast<NodeMeta*>(a + L.meta);
+  c.pool = reinterpret_cast<uint32_t*>(a + L.pool);
+  c.pending = reinterpret_cast<uint32_t*>(a + L.pending);
+  c.alloc_refs = reinterpret_cast<uint32_t*>(a + L.alloc_refs);
+  c.splits = reinterpret_cast<SplitEntry*>(a + L.splits);
+  c.sp_pt = reinterpret_cast<int4*>(a + L.sp_pt);
+  c.sp_gidx = reinterpret_cast<uint32_t*>(a + L.sp_gidx);
+  c.sp_cur = reinterpret_cast<uint32_t*>(a + L.sp_cur);
+  c.sp_slot = reinterpret_cast<uint32_t*>(a + L.sp_slot);
+  c.b_cur = reinterpret_cast<uint32_t*>(a + L.b_cur);
+  c.b_slot = reinterpret_cast<uint32_t*>(a + L.b_slot);
+  c.hash = reinterpret_cast<HSlot*>(a + L.hash);
+  c.keys = reinterpret_cast<uint2*>(a + L.keys);
+  c.staging = reinterpret_cast<int4*>(a + L.staging);
+  c.data = a + L.data;
+  c.data_bytes = L.data_bytes;
+  const simlod_config& g = h->cfg;
+  for (int k = 0; k < 3; ++k) c.rmin[k] = g.root_min[k];
+  c.rlog2 = g.root_log2;
+  c.T = g.leaf_capacity;
+  c.C = g.chunk_points;
+  c.G = g.grid_log2;
+  c.chunk_bytes = chunk_bytes_of(&g);
+  c.chunk_units = c.chunk_bytes / REF_BYTES;
+  c.grid_bytes = grid_bytes_of(&g);
+  c.hash_mask = (uint32_t)(L.hash_slots - 1);
+  c.max_nodes = (uint32_t)g.max_nodes;
+  c.max_chunks = (uint32_t)L.max_chunks;
+  c.spill_cap = (uint32_t)g.spill_capacity;
+  c.backlog_cap = (uint32_t)g.backlog_capacity;
+  c.max_splits = (uint32_t)L.max_splits;
+  c.max_batch = g.max_batch_points;
+}
+
+int error_from_bits(uint32_t e) {
+  if (e & E_ARENA) return SIMLOD_ERR_ARENA_FULL;
+  if (e & E_NODES) return SIMLOD_ERR_NODES_FULL;
+  if (e & E_SPILL) return SIMLOD_ERR_SPILL_FULL;
+  if (e & E_BACKLOG) return SIMLOD_ERR_BACKLOG_FULL;
+  if (e & (E_ALLOC_REFS | E_POOL)) return SIMLOD_ERR_ARENA_FULL;
+  return SIMLOD_ERR_CUDA;
+}
+
+int poison(simlod_t* h, int status) {
+  if (!h->sticky) h->sticky = status;
+  return status;
+}
+
+cudaEvent_t take_event(simlod_t* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Fold finished timing pairs into the per-kernel totals (after a sync).
+void harvest_timing(simlod_t* h) {
+  for (auto& p : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      h->ms[p.kernel] += ms;
+      h->launches[p.kernel] += 1;
+    }
+    h->ev_pool.push_back(p.a);
+    h->ev_pool.push_back(p.b);
+  }
+  h->pending.clear();
+}
+
+template <typename Launch>
+int launch(simlod_t* h, int kernel, cudaStream_t s, Launch&& fn) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (h->timing) {
+    a = take_event(h);
+    cudaEventRecord(a, s);
+  }
+  fn();
+  cudaError_t err = cudaGetLastError();
+  if (h->timing) {
+    b = take_event(h);
+    cudaEventRecord(b, s);
+    h->pending.push_back({kernel, a, b});
+  }
+  return err == cudaSuccess ? SIMLOD_OK : SIMLOD_ERR_CUDA;
+}
+
+unsigned grid_for(const simlod_t* h, uint64_t work, uint64_t per_block) {
+  uint64_t blocks = (work + per_block - 1) / per_block;
+  uint64_t cap = (uint64_t)h->sm_count * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (unsigned)blocks;
+}
+
+// Read the control block (waits for the stream).
+int read_ctl(simlod_t* h, cudaStream_t s) {
+  if (cudaMemcpyAsync(h->ctl_host, h->ctx.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    return SIMLOD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SIMLOD_ERR_CUDA;
+  if (h->timing) harvest_timing(h);
+  return SIMLOD_OK;
+}
+
+int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
+  h->last_stream = s;
+  const Ctx& c = h->ctx;
+  const unsigned long long base = h->base;
+  const uint32_t nodes0 = h->n_nodes;
+  const unsigned gp = grid_for(h, n, BLOCK);
+  int rc;
+  rc = launch(h, K_COUNT, s, [&] { k_count1<<<gp, BLOCK, 0, s>>>(c, pts, n, base); });
+  if (rc) return poison(h, rc);
+  rc = launch(h, K_DECIDE, s, [&] {
+    k_decide<<<grid_for(h, nodes0, BLOCK), BLOCK, 0, s>>>(c, 0, 0, 0, nodes0);
+  });
+  if (rc) return poison(h, rc);
+  if ((rc = read_ctl(h, s))) return poison(h, rc);
+  const Ctl& t = *h->ctl_host;
+  if (t.error) return poison(h, error_from_bits(t.error));
+  if (t.reject) {
+    rc = launch(h, K_OTHER, s, [&] { k_end_rejected<<<1, 1, 0, s>>>(c); });
+    if (rc) return poison(h, rc);
+    return SIMLOD_ERR_OUT_OF_BOUNDS;
+  }
+  const uint32_t max_iters = h->cfg.max_expand_iters ? h->cfg.max_expand_iters
+                                                      : h->cfg.root_log2 + 1;
+  uint32_t s_lo = 0, s_hi = t.split_count, n_lo = nodes0, n_hi = t.n_nodes, iters = 1;
+  while (s_hi > s_lo) {
+    if (iters >= max_iters) return poison(h, SIMLOD_ERR_ITER_CAP);
+    const uint32_t n_spill = h->ctl_host->spill_count;
+    rc = launch(h, K_SPILL, s, [&] {
+      k_spill<<<std::min<uint32_t>(s_hi - s_lo, 65535u), BLOCK, 0, s>>>(c, s_lo, s_hi);
+    });
+    if (rc) return poison(h, rc);
+    rc = launch(h, K_MERGE, s, [&] { k_merge_pending<<<1, 1024, 0, s>>>(c); });
+    if (rc) return poison(h, rc);
+    rc = launch(h, K_ADVANCE, s, [&] {
+      k_advance<<<grid_for(h, n + n_spill, BLOCK), BLOCK, 0, s>>>(c, pts, n, base, n_spill);
+    });
+    if (rc) return poison(h, rc);
+    const uint64_t cand = (uint64_t)(s_hi - s_lo) + (n_hi - n_lo);
+    rc = launch(h, K_DECIDE, s, [&] {
+      k_decide<<<grid_for(h, cand, BLOCK), BLOCK, 0, s>>>(c, s_lo, s_hi, n_lo, n_hi);
+    });
+    if (rc) return poison(h, rc);
+    if ((rc = read_ctl(h, s))) return poison(h, rc);
+    if (h->ctl_host->error) return poison(h, error_from_bits(h->ctl_host->error));
+    s_lo = s_hi;
+    s_hi = h->ctl_host->split_count;
+    n_lo = n_hi;
+    n_hi = h->ctl_host->n_nodes;
+    ++iters;
+  }
+  const uint32_t n_spill = h->ctl_host->spill_count;
+  const uint32_t n_keys = std::min<uint32_t>(h->ctl_host->nkeys, c.backlog_cap);
+  rc = launch(h, K_STORE, s, [&] {
+    k_store<<<grid_for(h, std::max<uint64_t>(n + n_spill, n_keys), BLOCK), BLOCK, 0, s>>>(
+        c, pts, n, base, n_spill, n_keys);
+  });
+  if (rc) return poison(h, rc);
+  rc = launch(h, K_END, s, [&] { k_end<<<1, 1, 0, s>>>(c, n, iters); });
+  if (rc) return poison(h, rc);
+  h->base += n;
+  h->n_nodes = h->ctl_host->n_nodes;
+  return SIMLOD_OK;
+}
+
+int init_octree(simlod_t* h, cudaStream_t s, bool clear_hash) {
+  const Ctx& c = h->ctx;
+  if (clear_hash) {
+    k_fill_hash<<<grid_for(h, h->lay.hash_slots, BLOCK), BLOCK, 0, s>>>(c.hash, h->lay.hash_slots);
+    if (cudaGetLastError() != cudaSuccess) return SIMLOD_ERR_CUDA;
+  }
+  k_init<<<1, 1, 0, s>>>(c);
+  if (cudaGetLastError() != cudaSuccess) return SIMLOD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SIMLOD_ERR_CUDA;
+  h->base = 0;
+  h->n_nodes = 1;
+  h->sticky = 0;
+  h->last_stream = s;
+  return SIMLOD_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+SIMLOD_API void simlod_config_default(simlod_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->root_log2 = 20;
+  cfg->leaf_capacity = 50000;
+  cfg->chunk_points = 1000;
+  cfg->grid_log2 = 7;
+  cfg->max_expand_iters = 0;
+  cfg->max_batch_points = 16ull << 20;
+  cfg->spill_capacity = 8ull << 20;
+  cfg->backlog_capacity = 10000000ull;
+  cfg->max_nodes = 1ull << 20;
+}
+
+SIMLOD_API int simlod_arena_bytes(const simlod_config* cfg, uint64_t data_bytes,
+                                  uint64_t* arena_bytes) {
+  if (!valid_config(cfg) || !arena_bytes) return SIMLOD_ERR_INVALID_ARG;
+  Layout L;
+  plan_layout(cfg, 0, &L);  // fixed part only
+  size_t o = L.staging + 16 * cfg->max_batch_points;
+  uint64_t chunks = data_bytes / chunk_bytes_of(cfg) + 1;
+  o = align_up(o, 256) + align_up(4 * chunks, 256) * 3 + 256;
+  *arena_bytes = align_up(o + data_bytes, 256) + 256;
+  return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t arena_bytes,
+                             void* stream, simlod_t** out) {
+  if (!out) return SIMLOD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!valid_config(cfg) || !d_arena || (reinterpret_cast<uintptr_t>(d_arena) & 255u))
+    return SIMLOD_ERR_INVALID_ARG;
+  simlod_t* h = new (std::nothrow) simlod_t();
+  if (!h) return SIMLOD_ERR_INVALID_ARG;
+  h->cfg = *cfg;
+  h->arena = static_cast<uint8_t*>(d_arena);
+  h->arena_bytes = arena_bytes;
+  if (!plan_layout(cfg, arena_bytes, &h->lay) || h->lay.max_chunks < 1) {
+    delete h;
+    return SIMLOD_ERR_INVALID_ARG;
+  }
+  make_ctx(h);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&h->ctl_host), sizeof(Ctl)) != cudaSuccess) {
+    delete h;
+    return SIMLOD_ERR_CUDA;
+  }
+  memset(h->ctl_host, 0, sizeof(Ctl));
+  int rc = init_octree(h, static_cast<cudaStream_t>(stream), true);
+  if (rc) {
+    cudaFreeHost(h->ctl_host);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_insert_batch(simlod_t* h, const simlod_point* d_pts, uint64_t n,
+                                   void* stream) {
+  if (!h) return SIMLOD_ERR_INVALID_ARG;
+  if (h->sticky) return SIMLOD_ERR_POISONED;
+  if (n == 0) return SIMLOD_OK;
+  if (!d_pts || (reinterpret_cast<uintptr_t>(d_pts) & 15u) || n > h->cfg.max_batch_points)
+    return SIMLOD_ERR_INVALID_ARG;
+  if (h->base + n > (1ull << 32)) return SIMLOD_ERR_TOO_MANY_POINTS;
+  return insert_device(h, reinterpret_cast<const int4*>(d_pts), n,
+                       static_cast<cudaStream_t>(stream));
+}
+
+SIMLOD_API int simlod_insert_batch_host(simlod_t* h, const simlod_point* h_pts, uint64_t n,
+                                        void* stream) {
+  if (!h) return SIMLOD_ERR_INVALID_ARG;
+  if (h->sticky) return SIMLOD_ERR_POISONED;
+  if (n == 0) return SIMLOD_OK;
+  if (!h_pts || n > h->cfg.max_batch_points) return SIMLOD_ERR_INVALID_ARG;
+  if (h->base + n > (1ull << 32)) return SIMLOD_ERR_TOO_MANY_POINTS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemcpyAsync(h->ctx.staging, h_pts, n * sizeof(simlod_point), cudaMemcpyHostToDevice,
+                      s) != cudaSuccess)
+    return poison(h, SIMLOD_ERR_CUDA);
+  return insert_device(h, h->ctx.staging, n, s);
+}
+
+SIMLOD_API int simlod_frame_update(simlod_t* h, const simlod_point* const* d_batches,
+                                   const uint64_t* counts, uint32_t n_batches,
+                                   uint64_t budget_ns, void* stream, uint32_t* consumed) {
+  if (!h || !consumed || (n_batches && (!d_batches || !counts))) return SIMLOD_ERR_INVALID_ARG;
+  *consumed = 0;
+  if (h->sticky) return SIMLOD_ERR_POISONED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
+    return SIMLOD_ERR_CUDA;
+  cudaEventRecord(t0, s);
+  int rc = SIMLOD_OK;
+  for (uint32_t k = 0; k < n_batches; ++k) {
+    if (k > 0) {
+      // Section 7.2: once the frame's budget is spent, stop and resume in the
+      // next frame; the check sits between batches.
+      cudaEventRecord(t1, s);
+      cudaEventSynchronize(t1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if ((double)ms * 1e6 > (double)budget_ns) break;
+    }
+    rc = simlod_insert_batch(h, d_batches[k], counts[k], stream);
+    if (rc) break;
+    *consumed = k + 1;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  return rc;
+}
+
+SIMLOD_API int simlod_reset(simlod_t* h, void* stream) {
+  if (!h) return SIMLOD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // a poisoned update may have left claims in the table
+  return init_octree(h, s, h->sticky != 0);
+}
+
+SIMLOD_API int simlod_sync(simlod_t* h) {
+  if (!h) return SIMLOD_ERR_INVALID_ARG;
+  if (h->sticky) return SIMLOD_ERR_POISONED;
+  int rc = read_ctl(h, h->last_stream);
+  if (rc) return poison(h, rc);
+  if (h->ctl_host->error) return poison(h, error_from_bits(h->ctl_host->error));
+  return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_get_stats(simlod_t* h, simlod_stats* out) {
+  if (!h || !out) return SIMLOD_ERR_INVALID_ARG;
+  memset(out, 0, sizeof(*out));
+  int rc = read_ctl(h, h->last_stream);
+  if (rc) return rc;
+  const Ctl& t = *h->ctl_host;
+  out->batches = t.st_batches;
+  out->points = t.st_points;
+  out->rejected_batches = t.st_rejected;
+  out->spilled = t.st_spilled;
+  out->splits = t.st_splits;
+  out->voxels = t.st_voxels;
+  out->iterations_max = t.st_iter_max;
+  out->rounds = t.st_rounds;
+  out->nodes = t.n_nodes;
+  out->chunks_bumped = t.chunks_bumped;
+  out->chunks_pool = t.pool_top > 0 ? (uint64_t)t.pool_top : 0;
+  out->arena_bytes = h->arena_bytes;
+  out->data_bytes = h->lay.data_bytes;
+  out->data_used = t.bump;
+  out->last_points = t.last_points;
+  out->last_spilled = t.last_spilled;
+  out->last_splits = t.last_splits;
+  out->last_voxels = t.last_voxels;
+  out->last_iterations = t.last_iters;
+  out->sticky_status = h->sticky;
+  out->device_error_bits = t.error;
+  return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_snapshot(simlod_t* h, simlod_snapshot_t* snap) {
+  if (!h || !snap) return SIMLOD_ERR_INVALID_ARG;
+  if (h->sticky) return SIMLOD_ERR_POISONED;
+  cudaStream_t s = h->last_stream;
+  int rc = read_ctl(h, s);
+  if (rc) return poison(h, rc);
+  const Ctl t = *h->ctl_host;
+  if (t.error) return poison(h, error_from_bits(t.error));
+  const uint32_t n = t.n_nodes;
+  std::vector<uint32_t> child(n), num(n);
+  std::vector<NodeMeta> meta(n);
+  std::vector<uint8_t> data(t.bump);
+  const Ctx& c = h->ctx;
+  if (cudaMemcpy(child.data(), c.child, 4ull * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(num.data(), c.num, 4ull * n, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(meta.data(), c.meta, sizeof(NodeMeta) * n, cudaMemcpyDeviceToHost) !=
+          cudaSuccess ||
+      (t.bump && cudaMemcpy(data.data(), c.data, t.bump, cudaMemcpyDeviceToHost) != cudaSuccess))
+    return poison(h, SIMLOD_ERR_CUDA);
+  uint64_t np = 0, nv = 0;
+  for (uint32_t i = 0; i < n; ++i) (child[i] == NONE ? np : nv) += num[i];
+  snap->n_nodes = n;
+  snap->n_points = np;
+  snap->n_voxels = nv;
+  if (!snap->nodes && !snap->points && !snap->voxels) return SIMLOD_OK;
+  if (!snap->nodes || snap->nodes_capacity < n || (np && (!snap->points ||
+      snap->points_capacity < np)) || (nv && (!snap->voxels || snap->voxels_capacity < nv)))
+    return SIMLOD_ERR_INVALID_ARG;
+  const uint32_t C = h->cfg.chunk_points, G = h->cfg.grid_log2;
+  struct Key {
+    uint32_t level, ix, iy, iz, id;
+  };
+  std::vector<Key> keys(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint32_t L = h->cfg.root_log2 - meta[i].level;
+    keys[i] = {meta[i].level,
+               (uint32_t)(((long long)meta[i].min[0] - h->cfg.root_min[0]) >> L),
+               (uint32_t)(((long long)meta[i].min[1] - h->cfg.root_min[1]) >> L),
+               (uint32_t)(((long long)meta[i].min[2] - h->cfg.root_min[2]) >> L), i};
+  }
+  std::sort(keys.begin(), keys.end(), [](const Key& a, const Key& b) {
+    if (a.level != b.level) return a.level < b.level;
+    if (a.ix != b.ix) return a.ix < b.ix;
+    if (a.iy != b.iy) return a.iy < b.iy;
+    return a.iz < b.iz;
+  });
+  const uint64_t chunk_bytes = chunk_bytes_of(&h->cfg);
+  uint64_t po = 0, vo = 0;
+  int bad = 0;
+  for (uint32_t k = 0; k < n; ++k) {
+    const uint32_t i = keys[k].id;
+    const NodeMeta& m = meta[i];
+    const bool inner = child[i] != NONE;
+    simlod_node_rec& r = snap->nodes[k];
+    r.level = m.level;
+    r.is_inner = inner ? 1u : 0u;
+    r.min[0] = m.min[0];
+    r.min[1] = m.min[1];
+    r.min[2] = m.min[2];
+    r.log2size = h->cfg.root_log2 - m.level;
+    r.n_points = inner ? 0 : num[i];
+    r.n_voxels = inner ? num[i] : 0;
+    // walk the linked list, as a renderer would (Listing 1)
+    uint64_t walked = 0, idx = 0;
+    for (uint32_t ref = m.head; ref != NONE && walked <= m.n_chunks; ++walked) {
+      const uint64_t off = (uint64_t)ref * REF_BYTES;
+      if (off + chunk_bytes > data.size()) {
+        bad = 1;
+        break;
+      }
+      const uint8_t* ch = data.data() + off;
+      const int4* recs = reinterpret_cast<const int4*>(ch + CHUNK_HEADER);
+      const uint32_t* aux = reinterpret_cast<const uint32_t*>(ch + CHUNK_HEADER + 16ull * C);
+      for (uint32_t q = 0; q < C && idx < num[i]; ++q, ++idx) {
+        const int4 v = recs[q];
+        if (inner) {
+          snap->voxels[vo + idx] = simlod_voxel_rec{aux[q], v.x, v.y, v.z, (uint32_t)v.w};
+        } else {
+          snap->points[po + idx] = simlod_point_rec{v.x, v.y, v.z, (uint32_t)v.w, aux[q]};
+        }
+      }
+      ref = *reinterpret_cast<const uint32_t*>(ch);
+    }
+    if (idx != num[i]) bad = 1;
+    r.n_chunks = walked;
+    if (inner) {
+      std::sort(snap->voxels + vo, snap->voxels + vo + num[i],
+                [](const simlod_voxel_rec& a, const simlod_voxel_rec& b) { return a.cell < b.cell; });
+      vo += num[i];
+    } else {
+      std::sort(snap->points + po, snap->points + po + num[i],
+                [](const simlod_point_rec& a, const simlod_point_rec& b) { return a.gidx < b.gidx; });
+      po += num[i];
+    }
+  }
+  (void)G;
+  return bad ? SIMLOD_ERR_CUDA : SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_set_timing(simlod_t* h, int enable, int clear) {
+  if (!h) return SIMLOD_ERR_INVALID_ARG;
+  if (clear) {
+    cudaStreamSynchronize(h->last_stream);
+    harvest_timing(h);
+    memset(h->launches, 0, sizeof(h->launches));
+    memset(h->ms, 0, sizeof(h->ms));
+  }
+  h->timing = enable != 0;
+  return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_get_timing(simlod_t* h, simlod_timing* out) {
+  if (!h || !out) return SIMLOD_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return SIMLOD_ERR_CUDA;
+  harvest_timing(h);
+  for (int k = 0; k < SIMLOD_N_KERNELS; ++k) {
+    out->name[k] = kKernelNames[k];
+    out->launches[k] = h->launches[k];
+    out->ms[k] = h->ms[k];
+  }
+  return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_destroy(simlod_t* h) {
+  if (!h) return SIMLOD_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->last_stream);
+  harvest_timing(h);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->ctl_host) cudaFreeHost(h->ctl_host);
+  delete h;
+  return SIMLOD_OK;
+}
+
+SIMLOD_API const char* simlod_status_string(int status) {
+  switch (status) {
+    case SIMLOD_OK: return "ok";
+    case SIMLOD_ERR_INVALID_ARG: return "invalid argument";
+    case SIMLOD_ERR_OUT_OF_BOUNDS: return "point outside the root cube: batch rejected";
+    case SIMLOD_ERR_ARENA_FULL: return "arena data region exhausted";
+    case SIMLOD_ERR_BACKLOG_FULL: return "voxel backlog capacity exceeded";
+    case SIMLOD_ERR_SPILL_FULL: return "spill buffer capacity exceeded";
+    case SIMLOD_ERR_ITER_CAP: return "expansion iteration cap reached";
+    case SIMLOD_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SIMLOD_ERR_POISONED: return "handle poisoned by an earlier device error";
+    case SIMLOD_ERR_CUDA: return "CUDA runtime error";
+    case SIMLOD_ERR_NODES_FULL: return "node table exhausted";
+    case SIMLOD_ERR_TOO_MANY_POINTS: return "more than 2^32 points in one octree";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

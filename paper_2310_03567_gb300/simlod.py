@@ -1,0 +1,315 @@
+"""ctypes binding of ``libsimlod.so`` (the C ABI in ``include/simlod.h``).
+
+Argument marshalling only: every step of the update runs in the library's
+CUDA kernels. PyTorch provides the device arena (a uint8 CUDA tensor the
+caller owns, like the paper's persistent buffer, Section 3.2) and streams.
+There is no CPU fallback: if the library cannot be loaded, importing the
+binding's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+LIB_PATH = _build.LIB_PATH
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_OUT_OF_BOUNDS = -2
+ERR_ARENA_FULL = -3
+ERR_BACKLOG_FULL = -4
+ERR_SPILL_FULL = -5
+ERR_ITER_CAP = -6
+ERR_TIMEOUT = -7
+ERR_POISONED = -8
+ERR_CUDA = -9
+ERR_NODES_FULL = -10
+ERR_TOO_MANY_POINTS = -11
+
+N_KERNELS = 8
+
+
+class SimlodError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("root_min", ctypes.c_int32 * 3), ("root_log2", ctypes.c_uint32),
+                ("leaf_capacity", ctypes.c_uint32), ("chunk_points", ctypes.c_uint32),
+                ("grid_log2", ctypes.c_uint32), ("max_expand_iters", ctypes.c_uint32),
+                ("max_batch_points", ctypes.c_uint64), ("spill_capacity", ctypes.c_uint64),
+                ("backlog_capacity", ctypes.c_uint64), ("max_nodes", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class NodeRec(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_uint32), ("is_inner", ctypes.c_uint32),
+                ("min", ctypes.c_int32 * 3), ("log2size", ctypes.c_uint32),
+                ("n_points", ctypes.c_uint64), ("n_voxels", ctypes.c_uint64),
+                ("n_chunks", ctypes.c_uint64)]
+
+
+class Snapshot_t(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_void_p), ("nodes_capacity", ctypes.c_uint64),
+                ("points", ctypes.c_void_p), ("points_capacity", ctypes.c_uint64),
+                ("voxels", ctypes.c_void_p), ("voxels_capacity", ctypes.c_uint64),
+                ("n_nodes", ctypes.c_uint64), ("n_points", ctypes.c_uint64),
+                ("n_voxels", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "batches", "points", "rejected_batches", "spilled", "splits", "voxels",
+        "iterations_max", "rounds", "nodes", "chunks_bumped", "chunks_pool", "arena_bytes", "data_bytes",
+        "data_used", "last_points", "last_spilled", "last_splits", "last_voxels",
+        "last_iterations")] + [("sticky_status", ctypes.c_int32),
+                               ("device_error_bits", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p * N_KERNELS), ("launches", ctypes.c_uint64 * N_KERNELS),
+                ("ms", ctypes.c_double * N_KERNELS)]
+
+
+# numpy views of the snapshot records (same layout as the C structs)
+NODE_DTYPE = np.dtype([("level", "<u4"), ("is_inner", "<u4"), ("min", "<i4", (3,)),
+                       ("log2size", "<u4"), ("n_points", "<u8"), ("n_voxels", "<u8"),
+                       ("n_chunks", "<u8")])
+POINT_REC_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("z", "<i4"), ("rgba", "<u4"),
+                            ("gidx", "<u4")])
+VOXEL_REC_DTYPE = np.dtype([("cell", "<u4"), ("x", "<i4"), ("y", "<i4"), ("z", "<i4"),
+                            ("rgba", "<u4")])
+
+_lib = None
+
+# (name, restype, argtypes) of every exported function
+_P, _U64, _I32, _U32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32
+SIGNATURES = {
+    "simlod_config_default": (None, [ctypes.POINTER(Config)]),
+    "simlod_arena_bytes": (_I32, [ctypes.POINTER(Config), _U64, ctypes.POINTER(_U64)]),
+    "simlod_create": (_I32, [ctypes.POINTER(Config), _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    "simlod_insert_batch": (_I32, [_P, _P, _U64, _P]),
+    "simlod_insert_batch_host": (_I32, [_P, _P, _U64, _P]),
+    "simlod_frame_update": (_I32, [_P, _P, _P, _U32, _U64, _P, ctypes.POINTER(_U32)]),
+    "simlod_reset": (_I32, [_P, _P]),
+    "simlod_sync": (_I32, [_P]),
+    "simlod_get_stats": (_I32, [_P, ctypes.POINTER(Stats)]),
+    "simlod_snapshot": (_I32, [_P, ctypes.POINTER(Snapshot_t)]),
+    "simlod_set_timing": (_I32, [_P, _I32, _I32]),
+    "simlod_get_timing": (_I32, [_P, ctypes.POINTER(Timing)]),
+    "simlod_destroy": (_I32, [_P]),
+    "simlod_status_string": (ctypes.c_char_p, [_I32]),
+}
+
+
+def load(path: str | None = None):
+    """Load (building first if needed) the CUDA library; raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    if path is None:
+        path = LIB_PATH
+        if not os.path.exists(path):
+            _build.build_library()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load().simlod_status_string(status).decode()
+    except Exception:
+        return f"status {status}"
+
+
+def default_config(**overrides) -> Config:
+    cfg = Config()
+    load().simlod_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k == "root_min":
+            for a in range(3):
+                cfg.root_min[a] = int(v[a])
+        else:
+            setattr(cfg, k, int(v))
+    return cfg
+
+
+def arena_bytes(cfg: Config, data_bytes: int) -> int:
+    out = ctypes.c_uint64()
+    rc = load().simlod_arena_bytes(ctypes.byref(cfg), data_bytes, ctypes.byref(out))
+    if rc != OK:
+        raise SimlodError(rc, "simlod_arena_bytes")
+    return int(out.value)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Snapshot:
+    """Canonical octree (numpy structured arrays, same fields as the oracle)."""
+
+    def __init__(self, nodes, points, voxels):
+        self.nodes, self.points, self.voxels = nodes, points, voxels
+
+    def node_slices(self):
+        po = np.concatenate([[0], np.cumsum(self.nodes["n_points"])]).astype(np.int64)
+        vo = np.concatenate([[0], np.cumsum(self.nodes["n_voxels"])]).astype(np.int64)
+        for k in range(len(self.nodes)):
+            yield (self.nodes[k], self.points[po[k]:po[k + 1]], self.voxels[vo[k]:vo[k + 1]])
+
+
+class Octree:
+    """One octree in a caller-owned device arena.
+
+    ``arena`` is a uint8 CUDA tensor (or an int device pointer with
+    ``arena_nbytes``); it must outlive the octree.
+    """
+
+    def __init__(self, cfg: Config, arena, stream=None, arena_nbytes: int | None = None):
+        self._lib = load()
+        self.cfg = cfg
+        self.arena = arena  # keep the tensor alive
+        if isinstance(arena, int):
+            ptr, nbytes = arena, int(arena_nbytes)
+        else:
+            ptr, nbytes = arena.data_ptr(), arena.numel() * arena.element_size()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self._lib.simlod_create(ctypes.byref(cfg), ptr, nbytes, _stream_ptr(stream),
+                                     ctypes.byref(h))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def insert(self, pts, stream=None, check: bool = True) -> int:
+        """Insert a batch from a CUDA tensor of 16-byte records (uint8 [n,16],
+        int32 [n,4] or any contiguous tensor of n*16 bytes)."""
+        nbytes = pts.numel() * pts.element_size()
+        if nbytes % 16:
+            raise ValueError("points must be 16-byte records")
+        rc = self._lib.simlod_insert_batch(self._h, pts.data_ptr(), nbytes // 16,
+                                           _stream_ptr(stream if stream is not None else self.stream))
+        if check and rc != OK:
+            raise SimlodError(rc, "simlod_insert_batch")
+        return rc
+
+    def insert_ptr(self, ptr: int, n: int, stream=None) -> int:
+        return self._lib.simlod_insert_batch(
+            self._h, ptr, n, _stream_ptr(stream if stream is not None else self.stream))
+
+    def insert_host(self, pts: np.ndarray, stream=None, check: bool = True) -> int:
+        """Insert a batch held in host memory (numpy array of 16-byte records
+        or a pinned CPU tensor)."""
+        if isinstance(pts, np.ndarray):
+            a = np.ascontiguousarray(pts)
+            ptr, n = a.ctypes.data, a.nbytes // 16
+        else:
+            ptr, n = pts.data_ptr(), pts.numel() * pts.element_size() // 16
+        rc = self._lib.simlod_insert_batch_host(
+            self._h, ptr, n, _stream_ptr(stream if stream is not None else self.stream))
+        if check and rc != OK:
+            raise SimlodError(rc, "simlod_insert_batch_host")
+        return rc
+
+    def frame_update(self, batches, budget_ns: int, stream=None) -> tuple[int, int]:
+        """Apply the batches (CUDA tensors) in order within a time budget;
+        returns (status, batches consumed)."""
+        n = len(batches)
+        ptrs = (ctypes.c_void_p * max(n, 1))(*[b.data_ptr() for b in batches])
+        counts = (ctypes.c_uint64 * max(n, 1))(
+            *[b.numel() * b.element_size() // 16 for b in batches])
+        consumed = ctypes.c_uint32()
+        rc = self._lib.simlod_frame_update(
+            self._h, ptrs, counts, n, budget_ns,
+            _stream_ptr(stream if stream is not None else self.stream), ctypes.byref(consumed))
+        return rc, int(consumed.value)
+
+    def reset(self, stream=None):
+        rc = self._lib.simlod_reset(self._h, _stream_ptr(stream if stream is not None else self.stream))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_reset")
+
+    def sync(self) -> int:
+        return self._lib.simlod_sync(self._h)
+
+    def stats(self) -> dict:
+        st = Stats()
+        rc = self._lib.simlod_get_stats(self._h, ctypes.byref(st))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_get_stats")
+        return st.as_dict()
+
+    def set_timing(self, enable: bool, clear: bool = False):
+        self._lib.simlod_set_timing(self._h, int(enable), int(clear))
+
+    def timing(self) -> dict:
+        t = Timing()
+        rc = self._lib.simlod_get_timing(self._h, ctypes.byref(t))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_get_timing")
+        return {t.name[k].decode(): (int(t.launches[k]), float(t.ms[k])) for k in range(N_KERNELS)}
+
+    def snapshot(self) -> Snapshot:
+        s = Snapshot_t()
+        rc = self._lib.simlod_snapshot(self._h, ctypes.byref(s))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_snapshot (sizes)")
+        nodes = np.zeros(s.n_nodes, NODE_DTYPE)
+        points = np.zeros(s.n_points, POINT_REC_DTYPE)
+        voxels = np.zeros(s.n_voxels, VOXEL_REC_DTYPE)
+        s.nodes, s.nodes_capacity = nodes.ctypes.data, len(nodes)
+        s.points, s.points_capacity = (points.ctypes.data if len(points) else None), len(points)
+        s.voxels, s.voxels_capacity = (voxels.ctypes.data if len(voxels) else None), len(voxels)
+        rc = self._lib.simlod_snapshot(self._h, ctypes.byref(s))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_snapshot")
+        return Snapshot(nodes, points, voxels)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.simlod_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def points_tensor(pts: np.ndarray, device="cuda"):
+    """Copy 16-byte point records to a uint8 [n, 16] CUDA tensor."""
+    import torch
+    a = np.ascontiguousarray(pts).view(np.uint8).reshape(-1, 16)
+    return torch.from_numpy(a).to(device)
+
+
+def make_arena(cfg: Config, data_bytes: int, device="cuda"):
+    """Allocate a uint8 CUDA tensor large enough for cfg and data_bytes."""
+    import torch
+    return torch.empty(arena_bytes(cfg, data_bytes), dtype=torch.uint8, device=device)
