@@ -162,16 +162,19 @@ SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t are
                              void* stream, simlod_t** out);
 
 /* Insert one batch of n points (Section 5): d_pts is a device pointer to n
- * 16-byte records (16-byte aligned) that stay unchanged until the call
- * returns. The batch is one complete update: expansion, voxel sampling,
+ * 16-byte records (16-byte aligned), read-only for the library. The batch is
+ * one complete update: expansion, voxel sampling,
  * chunk allocation and storing. Batches are applied in call order; the k-th
  * point ever accepted gets gidx k. n = 0 is a no-op.
  *
- * The work runs on `stream`. The call returns when the update is complete on
- * the device (the expansion rounds are steered from the host, one
- * device-to-host read of the control block per round). Returns
- * SIMLOD_ERR_OUT_OF_BOUNDS, with the octree and the gidx counter unchanged,
- * when any point lies outside the root cube. */
+ * The work runs on `stream`, in stream order after earlier work there. The
+ * expansion rounds are steered from the host: the call waits for the stream
+ * once per round (a read of the control block), then enqueues the final
+ * store and returns without waiting for it. d_pts must therefore stay valid
+ * and unchanged until `stream` has passed the insert (record an event or
+ * synchronise). Returns SIMLOD_ERR_OUT_OF_BOUNDS, with the octree and the
+ * gidx counter unchanged, when any point lies outside the root cube. Calls on
+ * one handle must be ordered: use one stream, or order the streams. */
 SIMLOD_API int simlod_insert_batch(simlod_t* h, const simlod_point* d_pts, uint64_t n,
                                    void* stream);
 

@@ -323,12 +323,13 @@ __device__ void phase_count1(const Ctx& c, const int4* pts, uint64_t n, unsigned
 // ----------------------------------------------------------- phase: advance
 
 // Later iterations: items whose cursor node split in the previous round
-// sample that node's fresh grid and count into the child below.
-__device__ __forceinline__ void advance_item(const Ctx& c, bool valid, int4 p, uint32_t gidx,
-                                             uint32_t* cur, uint32_t* slot_out) {
-  uint32_t node = valid ? *cur : 0;
-  uint32_t ch = valid ? c.child[node] : NONE;
-  bool moving = valid && ch != NONE;
+// sample that node's fresh grid and count into the child below. Returns true
+// when the item moved; its new cursor and slot are then in cur and slot.
+__device__ __forceinline__ bool advance_item(const Ctx& c, bool valid, int4 p, uint32_t gidx,
+                                             uint32_t& cur, uint32_t& slot) {
+  const uint32_t node = cur;
+  const uint32_t ch = valid ? c.child[node] : NONE;
+  const bool moving = valid && ch != NONE;
   uint32_t rx = 0, ry = 0, rz = 0, L = 0, cell = 0, nxt = 0;
   if (moving) {
     rel_coords(c, p, rx, ry, rz);
@@ -339,11 +340,12 @@ __device__ __forceinline__ void advance_item(const Ctx& c, bool valid, int4 p, u
   // the grid of a node split in this update is empty until store
   warp_claim(c, moving, ((unsigned long long)node << (3u * c.G)) | cell, gidx, (uint32_t)p.w,
              node);
-  uint32_t s = warp_count(c, moving, nxt);
+  const uint32_t s = warp_count(c, moving, nxt);
   if (moving) {
-    *cur = nxt;
-    *slot_out = s;
+    cur = nxt;
+    slot = s;
   }
+  return moving;
 }
 
 __device__ void phase_advance(const Ctx& c, const int4* pts, uint64_t n, unsigned long long base,
@@ -352,20 +354,24 @@ __device__ void phase_advance(const Ctx& c, const int4* pts, uint64_t n, unsigne
   const uint64_t wb = (n + 31) / 32, ws = (n_spill + 31ull) / 32;
   for (uint64_t w = warp0; w < wb + ws; w += nwarps) {
     if (w < wb) {
-      uint64_t i = w * 32 + lane;
-      bool valid = i < n;
-      int4 p = valid ? __ldg(pts + i) : make_int4(0, 0, 0, 0);
-      uint32_t dummy_cur = 0, dummy_slot = 0;
-      advance_item(c, valid, p, (uint32_t)(base + i), valid ? c.b_cur + i : &dummy_cur,
-                   valid ? c.b_slot + i : &dummy_slot);
+      const uint64_t i = w * 32 + lane;
+      const bool valid = i < n;
+      const int4 p = valid ? __ldg(pts + i) : make_int4(0, 0, 0, 0);
+      uint32_t cur = valid ? c.b_cur[i] : 0u, slot = 0;
+      if (advance_item(c, valid, p, (uint32_t)(base + i), cur, slot)) {
+        c.b_cur[i] = cur;
+        c.b_slot[i] = slot;
+      }
     } else {
-      uint64_t e = (w - wb) * 32 + lane;
-      bool valid = e < n_spill;
-      int4 p = valid ? c.sp_pt[e] : make_int4(0, 0, 0, 0);
-      uint32_t g = valid ? c.sp_gidx[e] : 0u;
-      uint32_t dummy_cur = 0, dummy_slot = 0;
-      advance_item(c, valid, p, g, valid ? c.sp_cur + e : &dummy_cur,
-                   valid ? c.sp_slot + e : &dummy_slot);
+      const uint64_t e = (w - wb) * 32 + lane;
+      const bool valid = e < n_spill;
+      const int4 p = valid ? c.sp_pt[e] : make_int4(0, 0, 0, 0);
+      const uint32_t g = valid ? c.sp_gidx[e] : 0u;
+      uint32_t cur = valid ? c.sp_cur[e] : 0u, slot = 0;
+      if (advance_item(c, valid, p, g, cur, slot)) {
+        c.sp_cur[e] = cur;
+        c.sp_slot[e] = slot;
+      }
     }
   }
 }

@@ -206,14 +206,29 @@ class Octree:
     def handle(self):
         return self._h
 
+    def _order(self, stream, tensor=None):
+        """Make `stream` wait for the caller's current stream (which produced
+        the batch) and keep `tensor` from being recycled before `stream` has
+        read it."""
+        s = stream if stream is not None else self.stream
+        if s is None or isinstance(s, int):
+            return s
+        import torch
+        cur = torch.cuda.current_stream()
+        if cur.cuda_stream != s.cuda_stream:
+            s.wait_stream(cur)
+            if tensor is not None:
+                tensor.record_stream(s)
+        return s
+
     def insert(self, pts, stream=None, check: bool = True) -> int:
         """Insert a batch from a CUDA tensor of 16-byte records (uint8 [n,16],
         int32 [n,4] or any contiguous tensor of n*16 bytes)."""
         nbytes = pts.numel() * pts.element_size()
         if nbytes % 16:
             raise ValueError("points must be 16-byte records")
-        rc = self._lib.simlod_insert_batch(self._h, pts.data_ptr(), nbytes // 16,
-                                           _stream_ptr(stream if stream is not None else self.stream))
+        s = self._order(stream, pts)
+        rc = self._lib.simlod_insert_batch(self._h, pts.data_ptr(), nbytes // 16, _stream_ptr(s))
         if check and rc != OK:
             raise SimlodError(rc, "simlod_insert_batch")
         return rc
@@ -240,6 +255,8 @@ class Octree:
         """Apply the batches (CUDA tensors) in order within a time budget;
         returns (status, batches consumed)."""
         n = len(batches)
+        for b in batches:
+            self._order(stream, b)
         ptrs = (ctypes.c_void_p * max(n, 1))(*[b.data_ptr() for b in batches])
         counts = (ctypes.c_uint64 * max(n, 1))(
             *[b.numel() * b.element_size() // 16 for b in batches])

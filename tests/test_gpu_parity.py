@@ -5,6 +5,8 @@ per-node voxel sets (cell, position, rgba) and per-leaf point multisets
 (x, y, z, rgba, gidx) must equal the oracle's byte for byte, after every batch
 on the small cases and at the end on the large ones.
 """
+import zlib
+
 import numpy as np
 import pytest
 
@@ -129,7 +131,7 @@ def _gen(kind, n, L, seed):
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_random_configs_every_batch(case):
     name, L, T, C, G, n, nb, kind = case
-    pts = _gen(kind, n, L, hash(name) % 1000)
+    pts = _gen(kind, n, L, zlib.crc32(name.encode()) % 1000)
     rng = np.random.default_rng(len(name))
     cuts = sorted(set(rng.integers(1, n, nb - 1).tolist()) | {0, n})
     kw = dict(root_log2=L, leaf_capacity=T, chunk_points=C, grid_log2=G)
@@ -235,7 +237,7 @@ def test_max_batch_size_and_determinism():
     n = 1 << 20
     pts = synth.uniform(17, 1 << 18, n)
     kw = dict(root_log2=18, leaf_capacity=2000, chunk_points=100, grid_log2=6,
-              max_batch_points=n)
+              max_batch_points=n, backlog_capacity=4 << 20)
     a = make_tree(1 << 30, **small_caps(**kw))
     b = make_tree(1 << 30, **small_caps(**kw))
     a.insert(simlod.points_tensor(pts))
@@ -284,7 +286,9 @@ def test_frame_budget_stops_between_batches():
 
 @pytest.mark.parametrize("what", ["arena", "nodes", "spill", "backlog", "iters"])
 def test_capacity_errors_poison_the_handle(what):
-    pts = synth.uniform(37, 1 << 16, 60_000)
+    # 20k-point batches into T = 200 leaves: the first batch builds leaves of
+    # ~40 points, which refill and split (spilling ~200 points each) by batch 6
+    pts = synth.uniform(37, 1 << 16, 200_000)
     kw = small_caps(root_log2=16, leaf_capacity=200, chunk_points=16, grid_log2=7)
     data = 256 << 20
     expect = {"arena": simlod.ERR_ARENA_FULL, "nodes": simlod.ERR_NODES_FULL,
