@@ -215,6 +215,40 @@ SIMLOD_API int simlod_snapshot(simlod_t* h, simlod_snapshot_t* snap);
 SIMLOD_API int simlod_set_timing(simlod_t* h, int enable, int clear);
 SIMLOD_API int simlod_get_timing(simlod_t* h, simlod_timing* out);
 
+/* Largest batch simlod_sample_node_noalloc accepts. */
+#define SIMLOD_NOALLOC_MAX_POINTS 131072u
+
+/* Voxel sampling of one node with no device allocation at all. The paper has
+ * no counterpart: it exists for callers that cannot allocate device memory
+ * when they need the step, such as a running real-time frame loop (cudaMalloc
+ * and cudaFree can synchronise the device and stall a frame) or code inside
+ * another framework that owns every device buffer and passes in only inputs
+ * and outputs. It needs no handle and no arena.
+ *
+ * Computes the voxels that the points d_pts[0..n) create in the 2^grid_log2
+ * grid inscribed in the cube [node_min, node_min + 2^log2size) per axis, the
+ * same way an update samples an inner node: one voxel per occupied cell, at
+ * the floor of the cell centre, coloured by the point with the lowest index.
+ * Points outside the cube are ignored. Writes the voxels, in no particular
+ * order, to d_voxels and their number to *d_count (both device memory owned
+ * by the caller; voxels_capacity >= min(n, 2^(3 grid_log2))). The work is
+ * enqueued on `stream`; nothing is waited for.
+ *
+ * Scratch lives in one fixed array of about 4.5 MiB per device, a file-scope
+ * device variable that every GPU loading this library holds until the
+ * process exits; hence n is limited to SIMLOD_NOALLOC_MAX_POINTS and larger
+ * batches are rejected with SIMLOD_ERR_INVALID_ARG. The first call on a device
+ * looks up that array's device address with the device current; make that
+ * first call before any stream capture. Every call clears and reuses the same
+ * array, so calls whose work overlaps on the GPU (different streams, other
+ * threads) race and must be serialised by the caller. Calls no cudaMalloc,
+ * cudaFree or allocating library routine. */
+SIMLOD_API int simlod_sample_node_noalloc(const simlod_point* d_pts, uint64_t n,
+                                          const int32_t node_min[3], uint32_t log2size,
+                                          uint32_t grid_log2, simlod_voxel_rec* d_voxels,
+                                          uint64_t voxels_capacity, uint32_t* d_count,
+                                          void* stream);
+
 /* Release host-side state. The arena is the caller's and is not touched. */
 SIMLOD_API int simlod_destroy(simlod_t* h);
 

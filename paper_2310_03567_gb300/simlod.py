@@ -108,6 +108,8 @@ SIGNATURES = {
     "simlod_get_timing": (_I32, [_P, ctypes.POINTER(Timing)]),
     "simlod_destroy": (_I32, [_P]),
     "simlod_status_string": (ctypes.c_char_p, [_I32]),
+    "simlod_sample_node_noalloc": (_I32, [_P, _U64, ctypes.POINTER(ctypes.c_int32), _U32, _U32,
+                                          _P, _U64, _P, _P]),
 }
 
 
