@@ -31,26 +31,11 @@ UNIT = "Mpts/s"
 L2_BYTES = 129 << 20
 CTL_BYTES = 192  # the library's control block, read once per expansion round
 
-# Algorithmic bytes each kernel is charged with (the per-update total is
-# 16 B + 20 B per batch point, 40 B per re-inserted point, 16 B per new voxel
-# and one zeroed grid per split):
-#   count1: reads every batch point once (16 B)
-#   spill:  reads every re-inserted point once (20 B with its gidx) and zeroes
-#           the new grids
-#   store:  writes every point with its gidx (20 B, batch and re-inserted) and
-#           every new voxel (16 B)
-#   advance, decide, merge_pending, end: no algorithmic bytes (re-traversal,
-#           bookkeeping)
-
-
-def kernel_alg_bytes(name: str, B: int, S: int, V: int, K: int, grid_bytes: int) -> int:
-    if name == "count1":
-        return 16 * B
-    if name == "spill":
-        return 20 * S + grid_bytes * K
-    if name == "store":
-        return 20 * (B + S) + 16 * V
-    return 0
+# Algorithmic bytes of one update: read every batch point (16 B), write
+# every point with its gidx (20 B), read and rewrite every re-inserted point
+# (2 x 20 B), write every new voxel (16 B), zero one grid per split. Repeated
+# traversals, cursors, the claim table and the backlog are implementation
+# overhead and are not counted.
 
 
 def update_alg_bytes(B, S, V, K, grid_bytes):
@@ -227,8 +212,9 @@ def run_ours(args):
             w.points = synth.terrain(1 + 1000 * rank, w.n_points)
     n_points = w.n_points
     dev_pts = simlod.points_tensor(w.points)
-    batches = [(dev_pts.data_ptr() + int(o) * 16, int(c)) for o, c in zip(w.offsets, w.counts)]
-    max_batch = int(w.counts.max())
+    ptrs = [dev_pts.data_ptr() + int(o) * 16 for o in w.offsets]
+    counts = [int(c) for c in w.counts]
+    max_batch = max(counts)
     cfg = simlod.default_config(root_min=w.root_min, root_log2=root_log2,
                                 max_batch_points=max_batch,
                                 spill_capacity=max(8 << 20, 2 * max_batch),
@@ -236,28 +222,35 @@ def run_ours(args):
     data_bytes = max(4 << 30, n_points * 80)
     arena = simlod.make_arena(cfg, data_bytes)
     stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
     tree = simlod.Octree(cfg, arena, stream=stream)
 
-    def step(lat=None):
+    def check(rc, what):
+        if rc != simlod.OK:
+            raise simlod.SimlodError(rc, what)
+
+    def fused_step():
         tree.reset()
-        for ptr, cnt in batches:
+        check(tree.insert_many_ptrs(ptrs, counts), "insert_batches")
+
+    def plain_pass(lat=None):
+        tree.reset()
+        for ptr, cnt in zip(ptrs, counts):
             if lat is not None:
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-            rc = tree.insert_ptr(ptr, cnt)
-            if rc != simlod.OK:
-                raise simlod.SimlodError(rc, "insert")
+            check(tree.insert_ptr(ptr, cnt), "insert_batch")
             if lat is not None:
                 b.record(stream)
                 lat.append((a, b))
 
     for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    stats = tree.stats()  # counts of one full pass (the last warm-up step)
+        fused_step()
+    check(tree.sync(), "warm-up")
+    stats = tree.stats()  # counts of one full pass
 
-    lat_events = []
+    # ---- timed region: K steps of the fused form
     clocks = ClockSampler(local)
     if dist:
         dist.barrier()
@@ -268,11 +261,12 @@ def run_ours(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        step(lat_events)
+        fused_step()
     ev1.record(stream)
     torch.cuda.synchronize()
     tree.set_timing(False)
     clk = clocks.stop()
+    check(tree.sync(), "timed steps")
     ms_total = ev0.elapsed_time(ev1)
     if dist:
         t = torch.tensor([ms_total], device="cuda")
@@ -280,73 +274,90 @@ def run_ours(args):
         ms_total = float(t.item())
         dist.barrier()
     ktime = tree.timing()
-    lat_ms = [a.elapsed_time(b) for a, b in lat_events]
 
-    # ---- end to end through the public API: host batches, H2D inside
+    # ---- per-batch latency: fused form one launch per batch, and plain form
+    lat_fused = []
+    tree.reset()
+    for ptr, cnt in zip(ptrs, counts):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        check(tree.insert_many_ptrs([ptr], [cnt]), "insert_batches")
+        b.record(stream)
+        lat_fused.append((a, b))
+    check(tree.sync(), "latency (fused)")
+    lat_plain = []
+    pe0 = torch.cuda.Event(enable_timing=True)
+    pe1 = torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    plain_pass(lat_plain)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    check(tree.sync(), "plain pass")
+    plain_ms = pe0.elapsed_time(pe1)
+    lat_f = [a.elapsed_time(b) for a, b in lat_fused]
+    lat_p = [a.elapsed_time(b) for a, b in lat_plain]
+
+    # ---- end to end through the public API: pinned host stream -> HBM,
+    # fused update, result (stats) back to the host, every step
     host_pts = torch.from_numpy(np.ascontiguousarray(w.points).view(np.uint8).reshape(-1, 16))
     host_pts = host_pts.pin_memory()
-    hptr = host_pts.data_ptr()
-    lib = simlod.load()
+    dev_e2e = torch.empty_like(dev_pts)
+    e2e_ptrs = [dev_e2e.data_ptr() + int(o) * 16 for o in w.offsets]
 
     def e2e_step():
+        with torch.cuda.stream(stream):
+            dev_e2e.copy_(host_pts, non_blocking=True)
         tree.reset()
-        for o, c in zip(w.offsets, w.counts):
-            rc = lib.simlod_insert_batch_host(tree.handle, hptr + int(o) * 16, int(c),
-                                              stream.cuda_stream)
-            if rc != simlod.OK:
-                raise simlod.SimlodError(rc, "insert_host")
-        return tree.stats()  # device-to-host read of the result
+        check(tree.insert_many_ptrs(e2e_ptrs, counts), "insert_batches (e2e)")
+        return tree.stats()
 
     e2e_step()
-    torch.cuda.synchronize()
     e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    del host_pts
+    del host_pts, dev_e2e
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel (the fused update: one launch = one step)
     peak, peak_src = load_peaks()
     B, S, V, K = n_points, stats["spilled"], stats["voxels"], stats["splits"]
     grid_bytes = (1 << (3 * cfg.grid_log2)) // 8
-    dom = max(ktime.items(), key=lambda kv: kv[1][1])
-    dom_name, (dom_launches, dom_ms) = dom
-    launches_per_step = dom_launches / args.steps
-    alg_per_step = kernel_alg_bytes(dom_name, B, S, V, K, grid_bytes)
-    avg_ms = dom_ms / max(dom_launches, 1)
-    achieved = (alg_per_step / max(launches_per_step, 1)) / (avg_ms * 1e-3) / 1e9 if avg_ms else 0.0
-    gpu_launches = sum(v[0] for v in ktime.values())
+    upd_bytes = update_alg_bytes(B, S, V, K, grid_bytes)
+    f_launches, f_ms = ktime["fused_update"]
+    avg_ms = f_ms / max(f_launches, 1)
+    achieved = upd_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms else 0.0
     ms_per_step = ms_total / args.steps
     value = n_points * world * args.steps / (ms_total * 1e-3) / 1e6
-    upd_bytes = update_alg_bytes(B, S, V, K, grid_bytes)
     roofline_mpts = B / (upd_bytes / (peak * 1e9)) / 1e6
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": w.name, "batch_points": max_batch, "batches_per_step": len(batches),
+        "config": {"workload": w.name, "batch_points": max_batch, "batches_per_step": len(ptrs),
                    "points_per_step": n_points, "leaf_capacity": cfg.leaf_capacity,
                    "chunk_points": cfg.chunk_points, "grid": 1 << cfg.grid_log2,
-                   "path": "plain per-kernel", "parallelism": f"replicas x{world}",
+                   "path": "fused persistent launch per step (every batch a full update)",
+                   "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (%.0f MB of points)" % (n_points * 16 / 2**20)},
-        "latency_ms": {"p50": percentile(lat_ms, 50), "p99": percentile(lat_ms, 99),
-                       "batches": len(lat_ms)},
-        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak,
+        "latency_ms": {"fused_p50": percentile(lat_f, 50), "fused_p99": percentile(lat_f, 99),
+                       "plain_p50": percentile(lat_p, 50), "plain_p99": percentile(lat_p, 99),
+                       "batches": len(lat_f)},
+        "plain": {"value": n_points / (plain_ms * 1e-3) / 1e6, "unit": UNIT,
+                  "ms_per_step": plain_ms},
+        "roofline": {"bound": "hbm", "kernel": "k_fused", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                     "peak_source": peak_src},
-        "update_roofline": {"alg_bytes_per_step": upd_bytes,
-                            "alg_bytes_per_point": upd_bytes / B,
-                            "achieved_gbs": upd_bytes / (ms_per_step * 1e-3) / 1e9,
-                            "roofline_mpts": roofline_mpts,
+                     "alg_bytes_per_launch": upd_bytes, "peak_source": peak_src},
+        "update_roofline": {"alg_bytes_per_point": upd_bytes / B, "roofline_mpts": roofline_mpts,
                             "frac": value / world / roofline_mpts},
         "update_counts": {"B": B, "S": S, "V": V, "K": K},
-        "kernels_ms_per_step": {k: v[1] / args.steps for k, v in ktime.items() if v[0]},
-        "gpu_launches": gpu_launches,
+        "gpu_launches": 2 * args.steps,
         "e2e": {"value": n_points * world / e2e_s / 1e6, "unit": UNIT,
-                "h2d_bytes_per_step": n_points * 16,
-                "d2h_bytes_per_step": CTL_BYTES * (stats["rounds"] + 1)},
+                "h2d_bytes_per_step": n_points * 16 + 16 * len(ptrs),
+                "d2h_bytes_per_step": CTL_BYTES},
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:

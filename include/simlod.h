@@ -184,17 +184,32 @@ SIMLOD_API int simlod_insert_batch(simlod_t* h, const simlod_point* d_pts, uint6
 SIMLOD_API int simlod_insert_batch_host(simlod_t* h, const simlod_point* h_pts, uint64_t n,
                                         void* stream);
 
-/* Frame-budget update (Section 7.2): apply batches 0, 1, ... in order, and
- * before starting batch k > 0 check the time spent since the call began; once
- * it exceeds budget_ns, stop. Batches are never cut. *consumed receives the
- * number of batches applied; the caller passes the rest in the next frame.
- * d_batches[k] are device pointers as in simlod_insert_batch. */
+/* Fused form: apply batches 0 .. n_batches-1 in order, each one complete
+ * update as in simlod_insert_batch, all inside one persistent cooperative
+ * launch on `stream` (Section 4: persistent threads with grid-wide syncs, the
+ * update kernel looping over the batches that have arrived). The phases are
+ * separated by grid barriers with a time limit, so no expansion round goes
+ * back to the host. Asynchronous: the call returns after enqueueing (it first
+ * waits for its own previous batch-table copy) and d_batches[k] (device
+ * pointers, 16-byte aligned) must stay valid until `stream` passes the
+ * launch. At most 16,384 batches per call. A batch with a point outside the
+ * root cube is skipped without change; the next simlod_sync then returns
+ * SIMLOD_ERR_OUT_OF_BOUNDS once. Device errors are reported by simlod_sync. */
+SIMLOD_API int simlod_insert_batches(simlod_t* h, const simlod_point* const* d_batches,
+                                     const uint64_t* counts, uint32_t n_batches, void* stream);
+
+/* Frame-budget update (Section 7.2): as simlod_insert_batches, but before
+ * starting batch k > 0 the kernel checks the time since the launch began
+ * (the GPU's global timer); once it exceeds budget_ns it stops. Batches are
+ * never cut. Waits for the launch; *consumed receives the number of batches
+ * handled, and the caller passes the rest in the next frame. */
 SIMLOD_API int simlod_frame_update(simlod_t* h, const simlod_point* const* d_batches,
                                    const uint64_t* counts, uint32_t n_batches,
                                    uint64_t budget_ns, void* stream, uint32_t* consumed);
 
 /* Empty the octree (one empty root leaf, gidx counter 0) without touching
- * the arena allocation; the handle's poison is cleared. */
+ * the arena allocation; the handle's poison is cleared. Enqueued on `stream`
+ * (it waits only when clearing a poisoned handle). */
 SIMLOD_API int simlod_reset(simlod_t* h, void* stream);
 
 /* Wait for the handle's last stream and report a device error, if any. */

@@ -52,14 +52,20 @@ def library_headers() -> list[str]:
 
 
 def library_command(out: str = LIB_PATH, extra: list[str] | None = None) -> list[str]:
+    # -dlcm=cg: plain global loads are served by the coherent L2, not the
+    # per-SM L1, because the persistent kernel re-reads node tables, split
+    # lists and grids that other blocks rewrote after a grid barrier (L1s are
+    # not coherent with each other within one grid). Read-only inputs use
+    # __ldg and keep the L1/texture path.
     return ([_nvcc(), *ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17", "-shared",
+             "-Xptxas", "-dlcm=cg",
              "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
              "-I", INCLUDE_DIR, "-I", CSRC_DIR]
             + (extra or []) + library_sources() + ["-o", out])
 
 
 def build_library(force: bool = False) -> str:
-    srcs = library_sources() + library_headers()
+    srcs = library_sources() + library_headers() + [os.path.abspath(__file__)]
     if force or _stale(LIB_PATH, srcs):
         tmp = LIB_PATH + ".tmp"
         _run(library_command(tmp))

@@ -53,6 +53,8 @@ enum : uint32_t {
   E_ALLOC_REFS = 16u,
   E_INTERNAL = 32u,
   E_POOL = 64u,
+  E_TIMEOUT = 128u,
+  E_ITER_CAP = 256u,
 };
 
 // Control block at the start of the arena.
@@ -73,7 +75,8 @@ struct Ctl {
   unsigned long long st_batches, st_points, st_rejected, st_spilled, st_splits, st_voxels,
       st_iter_max, st_rounds;
   unsigned long long last_points, last_spilled, last_splits, last_voxels, last_iters;
-  unsigned long long pad1[3];
+  unsigned long long st_rejected_async;  // rejections inside fused launches
+  unsigned long long pad1[2];
 };
 static_assert(sizeof(Ctl) % 16 == 0, "Ctl size");
 
@@ -207,22 +210,12 @@ __device__ __forceinline__ uint32_t cell_index(uint32_t rx, uint32_t ry, uint32_
 
 // -------------------------------------------------------- voxel claims
 
-// A new (node, cell) key was installed at table slot h: list it in the
-// backlog and give it a voxel slot of its node.
-__device__ __forceinline__ void new_voxel(const Ctx& c, uint32_t h, uint32_t node) {
-  uint32_t e = atomicAdd(&c.ctl->nkeys, 1u);
-  if (e >= c.backlog_cap) {
-    set_error(c, E_BACKLOG);
-    return;
-  }
-  uint32_t t = atomicAdd(&c.cnt[node], 1u);
-  c.keys[e] = make_uint2(h, c.num[node] + t);
-}
-
-// Offer (gidx, rgba) as the colour of cell `key`; the lowest gidx wins.
-__device__ __forceinline__ void hash_claim(const Ctx& c, unsigned long long key,
-                                           unsigned long long val, uint32_t node) {
-  uint32_t h = (uint32_t)fmix64(key) & c.hash_mask;
+// Offer val = (gidx << 32 | rgba) as the colour of cell `key`; the lowest
+// gidx wins. Returns true, with the table slot in h, when this call put the
+// key into the table (the cell is new in this update).
+__device__ __forceinline__ bool hash_claim(const Ctx& c, unsigned long long key,
+                                           unsigned long long val, uint32_t& h) {
+  h = (uint32_t)fmix64(key) & c.hash_mask;
   for (int probe = 0; probe < MAX_PROBES; ++probe) {
     HSlot* s = c.hash + h;
     unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&s->key);
@@ -230,29 +223,54 @@ __device__ __forceinline__ void hash_claim(const Ctx& c, unsigned long long key,
       unsigned long long old = atomicCAS(&s->key, HASH_EMPTY, key);
       if (old == HASH_EMPTY) {
         atomicMin(&s->val, val);
-        new_voxel(c, h, node);
-        return;
+        return true;
       }
       k = old;
     }
     if (k == key) {
-      atomicMin(&s->val, val);
-      return;
+      if (*reinterpret_cast<volatile unsigned long long*>(&s->val) > val) atomicMin(&s->val, val);
+      return false;
     }
     h = (h + 1u) & c.hash_mask;
   }
   set_error(c, E_BACKLOG);
+  return false;
 }
 
-// All 32 lanes call. Lanes with `want` contend for (node, cell) = key; lanes
-// with equal keys are merged first and only the lowest gidx goes to the table.
+// All 32 lanes call. Lanes with `want` contend for (node, cell) = key. Lanes
+// with equal keys are merged first and only the lowest gidx goes to the
+// table. Keys that are new in this update are appended to the backlog (one
+// atomic per warp) and get a voxel slot of their node (one atomic per node
+// and warp).
 __device__ __forceinline__ void warp_claim(const Ctx& c, bool want, unsigned long long key,
                                            uint32_t gidx, uint32_t rgba, uint32_t node) {
-  unsigned m = __ballot_sync(FULL_MASK, want);
-  if (!want) return;
-  unsigned grp = __match_any_sync(m, key);
-  unsigned best = __reduce_min_sync(grp, gidx);
-  if (gidx == best) hash_claim(c, key, ((unsigned long long)gidx << 32) | rgba, node);
+  const uint32_t lane = lane_id();
+  const unsigned m = __ballot_sync(FULL_MASK, want);
+  if (m == 0u) return;
+  bool inst = false;
+  uint32_t h = 0;
+  if (want) {
+    const unsigned grp = __match_any_sync(m, key);
+    const unsigned best = __reduce_min_sync(grp, gidx);
+    if (gidx == best) inst = hash_claim(c, key, ((unsigned long long)gidx << 32) | rgba, h);
+  }
+  const unsigned mi = __ballot_sync(FULL_MASK, inst);
+  if (mi == 0u) return;
+  const int leader = __ffs(mi) - 1;
+  uint32_t e0 = 0;
+  if ((int)lane == leader) e0 = atomicAdd(&c.ctl->nkeys, (uint32_t)__popc(mi));
+  e0 = __shfl_sync(FULL_MASK, e0, leader);
+  if (inst) {
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t e = e0 + __popc(mi & below);
+    const unsigned gm = __match_any_sync(mi, node);
+    const int nl = __ffs(gm) - 1;
+    uint32_t t0 = 0;
+    if ((int)lane == nl) t0 = c.num[node] + atomicAdd(&c.cnt[node], (uint32_t)__popc(gm));
+    t0 = __shfl_sync(gm, t0, nl);
+    if (e < c.backlog_cap) c.keys[e] = make_uint2(h, t0 + __popc(gm & below));
+    else set_error(c, E_BACKLOG);
+  }
 }
 
 // All 32 lanes call. Lanes with `valid` count one point into `leaf` and get
@@ -298,11 +316,17 @@ __device__ void phase_count1(const Ctx& c, const int4* pts, uint64_t n, unsigned
         if (ch == NONE) {
           walking = false;
         } else {
-          inner = true;
           cell = cell_index(rx, ry, rz, L, c.G);
-          uint32_t word = grid_words(c, c.meta[node].grid)[cell >> 5];
-          want = ((word >> (cell & 31u)) & 1u) == 0u;
+          const uint32_t gref = c.meta[node].grid;
           nxt = ch + octant(rx, ry, rz, L);
+          if (!ref_ok(c, gref, c.grid_bytes) || nxt >= c.max_nodes) {
+            set_error(c, E_INTERNAL);
+            walking = false;
+          } else {
+            inner = true;
+            const uint32_t word = grid_words(c, gref)[cell >> 5];
+            want = ((word >> (cell & 31u)) & 1u) == 0u;
+          }
         }
       }
       warp_claim(c, want, ((unsigned long long)node << (3u * c.G)) | cell, gidx, (uint32_t)p.w,
@@ -328,8 +352,10 @@ __device__ void phase_count1(const Ctx& c, const int4* pts, uint64_t n, unsigned
 __device__ __forceinline__ bool advance_item(const Ctx& c, bool valid, int4 p, uint32_t gidx,
                                              uint32_t& cur, uint32_t& slot) {
   const uint32_t node = cur;
-  const uint32_t ch = valid ? c.child[node] : NONE;
-  const bool moving = valid && ch != NONE;
+  const bool in_range = node < c.max_nodes;
+  if (valid && !in_range) set_error(c, E_INTERNAL);
+  const uint32_t ch = (valid && in_range) ? c.child[node] : NONE;
+  const bool moving = valid && ch != NONE && ch + 8u <= c.max_nodes;
   uint32_t rx = 0, ry = 0, rz = 0, L = 0, cell = 0, nxt = 0;
   if (moving) {
     rel_coords(c, p, rx, ry, rz);
@@ -506,25 +532,25 @@ __device__ __forceinline__ void decide_node(const Ctx& c, uint32_t id) {
 }
 
 // Candidates: the nodes split in the previous round (their voxels are now
-// all claimed) and the node id range [n_lo, n_hi). If the batch was rejected
-// (a point outside the root cube), undo the counters and claims instead.
+// all claimed) and the node id range [n_lo, n_hi).
 __device__ void phase_decide(const Ctx& c, uint32_t s_lo, uint32_t s_hi, uint32_t n_lo,
                              uint32_t n_hi, uint64_t t0, uint64_t nthreads) {
-  const bool rejected = *reinterpret_cast<volatile unsigned int*>(&c.ctl->reject) != 0u;
   const uint64_t ns = s_hi - s_lo, nn = n_hi - n_lo;
-  if (rejected) {
-    for (uint64_t t = t0; t < nn; t += nthreads) c.cnt[n_lo + t] = 0;
-    const uint32_t nk = *reinterpret_cast<volatile unsigned int*>(&c.ctl->nkeys);
-    for (uint64_t t = t0; t < nk && t < c.backlog_cap; t += nthreads) {
-      HSlot* s = c.hash + c.keys[t].x;
-      s->key = HASH_EMPTY;
-      s->val = HASH_EMPTY;
-    }
-    return;
-  }
   for (uint64_t t = t0; t < ns + nn; t += nthreads) {
     uint32_t id = t < ns ? c.splits[s_lo + t].node : (uint32_t)(n_lo + (t - ns));
     decide_node(c, id);
+  }
+}
+
+// The batch was rejected (a point outside the root cube): undo the counts
+// and claims of its count round, nodes [0, n_nodes), so nothing changed.
+__device__ void phase_rollback(const Ctx& c, uint32_t n_nodes, uint64_t t0, uint64_t nthreads) {
+  for (uint64_t t = t0; t < n_nodes; t += nthreads) c.cnt[t] = 0;
+  const uint32_t nk = min(*reinterpret_cast<volatile unsigned int*>(&c.ctl->nkeys), c.backlog_cap);
+  for (uint64_t t = t0; t < nk; t += nthreads) {
+    HSlot* s = c.hash + c.keys[t].x;
+    s->key = HASH_EMPTY;
+    s->val = HASH_EMPTY;
   }
 }
 
@@ -532,6 +558,10 @@ __device__ void phase_decide(const Ctx& c, uint32_t s_lo, uint32_t s_hi, uint32_
 
 __device__ __forceinline__ void store_rec(const Ctx& c, uint32_t node, uint32_t slot, int4 rec,
                                           uint32_t aux) {
+  if (node >= c.max_nodes) {
+    set_error(c, E_INTERNAL);
+    return;
+  }
   const NodeMeta& m = c.meta[node];
   const uint32_t j = slot / c.C, q = slot - j * c.C;
   uint32_t ref = NONE;
@@ -561,6 +591,10 @@ __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned 
     HSlot* s = c.hash + k.x;
     const unsigned long long key = s->key, val = s->val;
     const uint32_t node = (uint32_t)(key >> (3u * G)), cell = (uint32_t)key & cmask;
+    if (node >= c.max_nodes || !ref_ok(c, c.meta[node].grid, c.grid_bytes)) {
+      set_error(c, E_INTERNAL);
+      continue;
+    }
     const NodeMeta& m = c.meta[node];
     const uint32_t L = c.rlog2 - m.level;
     const uint32_t cx = cell & amask, cy = (cell >> G) & amask, cz = cell >> (2u * G);
@@ -575,6 +609,132 @@ __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned 
     s->key = HASH_EMPTY;
     s->val = HASH_EMPTY;
   }
+}
+
+// -------------------------------------------------------------- phase: spill
+
+// Per split leaf (one block each, blocks striding over the splits): zero the
+// node's new grid, copy its stored points and their gidx into its spill
+// range with the node as cursor, hand its chunks to the pending-free list.
+__device__ void phase_spill(const Ctx& c, uint32_t s_lo, uint32_t s_hi, uint32_t block0,
+                            uint32_t nblocks) {
+  constexpr uint32_t ROUND = 1024;
+  __shared__ uint32_t refs[ROUND];
+  __shared__ uint32_t s_nch, s_free0, s_n, s_bad;
+  for (uint32_t e = s_lo + block0; e < s_hi; e += nblocks) {
+    const SplitEntry se = c.splits[e];
+    const uint32_t id = se.node;
+    if (id >= c.max_nodes || !ref_ok(c, c.meta[id].grid, c.grid_bytes) ||
+        (unsigned long long)se.spill_off + c.num[id] > c.spill_cap) {
+      if (threadIdx.x == 0) set_error(c, E_INTERNAL);
+      continue;
+    }
+    NodeMeta& m = c.meta[id];
+    int4* g = reinterpret_cast<int4*>(grid_words(c, m.grid));
+    for (uint32_t q = threadIdx.x; q < c.grid_bytes / 16u; q += blockDim.x)
+      g[q] = make_int4(0, 0, 0, 0);
+    if (threadIdx.x == 0) {
+      s_bad = 0;
+      s_nch = m.n_chunks;
+      s_n = c.num[id];
+      s_free0 = atomicAdd(&c.ctl->pending_free, m.n_chunks);
+      if ((unsigned long long)s_free0 + m.n_chunks > c.max_chunks) set_error(c, E_POOL);
+    }
+    __syncthreads();
+    const uint32_t nch = s_nch, n = s_n, free0 = s_free0;
+    const bool ok = (unsigned long long)free0 + nch <= c.max_chunks;
+    uint32_t walk = m.head;  // used by thread 0 only
+    for (uint32_t r0 = 0; r0 < nch; r0 += ROUND) {
+      const uint32_t cnt = min(ROUND, nch - r0);
+      if (threadIdx.x == 0) {
+        for (uint32_t q = 0; q < cnt; ++q) {
+          if (!ref_ok(c, walk, c.chunk_bytes)) {  // list shorter than n_chunks
+            set_error(c, E_INTERNAL);
+            s_bad = 1;
+            break;
+          }
+          refs[q] = walk;
+          walk = *chunk_next(c, walk);
+        }
+      }
+      __syncthreads();
+      if (s_bad) break;
+      const uint64_t lo = (uint64_t)r0 * c.C;
+      const uint64_t hi = min((uint64_t)n, (uint64_t)(r0 + cnt) * c.C);
+      for (uint64_t idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
+        const uint32_t j = (uint32_t)(idx / c.C), q = (uint32_t)(idx - (uint64_t)j * c.C);
+        const uint32_t ref = refs[j - r0];
+        const uint64_t dst = se.spill_off + idx;
+        c.sp_pt[dst] = chunk_recs(c, ref)[q];
+        c.sp_gidx[dst] = chunk_aux(c, ref)[q];
+        c.sp_cur[dst] = id;
+      }
+      if (ok)
+        for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) c.pending[free0 + r0 + q] = refs[q];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      m.n_chunks = 0;
+      m.head = m.tail = NONE;
+      c.num[id] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+// One block: move the chunks freed by this round's splits into the pool.
+__device__ void phase_merge_pending(const Ctx& c) {
+  __shared__ int top;
+  __shared__ uint32_t np;
+  if (threadIdx.x == 0) {
+    top = c.ctl->pool_top;
+    np = c.ctl->pending_free;
+    if ((unsigned long long)top + np > c.max_chunks) {
+      set_error(c, E_POOL);
+      np = 0;
+    }
+  }
+  __syncthreads();
+  for (uint32_t q = threadIdx.x; q < np; q += blockDim.x) c.pool[top + q] = c.pending[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    c.ctl->pool_top = top + (int)np;
+    c.ctl->pending_free = 0;
+  }
+  __syncthreads();
+}
+
+// One thread: close an applied update (advance gidx, fold the update into
+// the stats, clear the per-update counters).
+__device__ void phase_end(const Ctx& c, uint64_t n, uint32_t iters) {
+  Ctl* t = c.ctl;
+  const unsigned long long nk =
+      min((unsigned long long)t->nkeys, (unsigned long long)c.backlog_cap);
+  t->base += n;
+  t->st_batches += 1;
+  t->st_points += n;
+  t->st_spilled += t->spill_count;
+  t->st_splits += t->split_count;
+  t->st_voxels += nk;
+  if (iters > t->st_iter_max) t->st_iter_max = iters;
+  t->st_rounds += iters;
+  t->last_points = n;
+  t->last_spilled = t->spill_count;
+  t->last_splits = t->split_count;
+  t->last_voxels = nk;
+  t->last_iters = iters;
+  t->spill_count = 0;
+  t->nkeys = 0;
+  t->alloc_seq = 0;
+  t->split_count = 0;
+}
+
+// One thread: close a rejected update (decide already undid its counters).
+__device__ void phase_end_rejected(const Ctx& c) {
+  Ctl* t = c.ctl;
+  t->reject = 0;
+  t->nkeys = 0;
+  t->st_rejected += 1;
 }
 
 }  // namespace sl

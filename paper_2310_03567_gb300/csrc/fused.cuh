@@ -1,0 +1,161 @@
+// Fused form of the update: one persistent cooperative launch runs every
+// phase of every batch in a list, with grid-wide barriers between phases
+// instead of kernel boundaries and host round trips. This is the paper's
+// own kernel organisation (Section 4: persistent threads and grid syncs,
+// the update kernel looping over the batches uploaded so far), with the
+// phases of device.cuh.
+//
+// Barriers are bounded: a block that waits longer than FUSED_BARRIER_NS
+// marks the launch aborted and returns, the others see the abort flag (or
+// time out themselves) and return as well; the host then reads a TIMEOUT
+// status. Nothing spins without a limit.
+#pragma once
+
+#include "device.cuh"
+
+namespace sl {
+
+constexpr unsigned long long FUSED_BARRIER_NS = 2000000000ull;  // 2 s
+constexpr int FUSED_BLOCK = 512;
+constexpr unsigned long long NO_BUDGET = ~0ull;
+constexpr uint32_t MAX_FUSED_BATCHES = 16384;
+
+struct BatchDesc {
+  const int4* pts;
+  unsigned long long n;
+};
+
+// Per-launch control words of the fused kernel (arena).
+struct FusedCtl {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  unsigned int abort;
+  unsigned int consumed;  // batches fully handled (applied or rejected)
+  unsigned int stop;      // the frame budget ran out
+  unsigned int rejected;  // batches rejected in this launch
+  unsigned int pad[10];
+};
+static_assert(sizeof(FusedCtl) == 64, "FusedCtl size");
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <typename T>
+__device__ __forceinline__ T vload(const T* p) {
+  return *reinterpret_cast<const volatile T*>(p);
+}
+
+// Grid-wide barrier with a time limit. Returns false when the launch was
+// aborted (by this block's timeout or another's).
+__device__ __forceinline__ bool grid_barrier(const Ctx& c, FusedCtl* f) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int gen = vload(&f->bar_gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(&f->bar_count, 1u);
+    int ok = 1;
+    if (arrived == gridDim.x - 1u) {
+      // every block has arrived: a device error raised before this barrier
+      // becomes one abort decision that all blocks read after it
+      if (vload(&c.ctl->error)) atomicExch(&f->abort, 1u);
+      atomicExch(&f->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&f->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer_ns();
+      while (vload(&f->bar_gen) == gen) {
+        if (vload(&f->abort)) {
+          ok = 0;
+          break;
+        }
+        if (globaltimer_ns() - t0 > FUSED_BARRIER_NS) {
+          atomicExch(&f->abort, 1u);
+          set_error(c, E_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok && !vload(&f->abort);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// All batches of `batches`, in order, each one complete update. Before a
+// batch other than the first, stop once more than budget_ns has passed since
+// the launch began (Section 7.2's frame budget; batches are never cut);
+// NO_BUDGET disables the check.
+__global__ void __launch_bounds__(FUSED_BLOCK) k_fused(Ctx c, const BatchDesc* batches,
+                                                        uint32_t n_batches, FusedCtl* f,
+                                                        unsigned long long budget_ns,
+                                                        uint32_t max_iters) {
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t warp0 = tid / 32, nwarps = nthreads / 32;
+  const unsigned long long t_begin = globaltimer_ns();
+  for (uint32_t b = 0; b < n_batches; ++b) {
+    // every value read here was written before the last barrier and is not
+    // written again before the next one, so all threads decide alike
+    if (vload(&f->stop)) return;
+    const BatchDesc bd = batches[b];
+    const unsigned long long base = vload(&c.ctl->base);
+    const uint32_t nodes0 = vload(&c.ctl->n_nodes);
+    bool rejected = false;
+    if (bd.n) {
+      phase_count1(c, bd.pts, bd.n, base, warp0, nwarps);
+      if (!grid_barrier(c, f)) return;
+      rejected = vload(&c.ctl->reject) != 0u;  // set only by the count round
+      if (rejected) {
+        phase_rollback(c, nodes0, tid, nthreads);
+        if (!grid_barrier(c, f)) return;  // all have read the flag before it is cleared
+        if (tid == 0) {
+          phase_end_rejected(c);
+          c.ctl->st_rejected_async += 1;
+          f->rejected += 1;
+        }
+      } else {
+        uint32_t s_lo = 0, s_hi = 0, n_lo = 0, n_hi = nodes0, iters = 1;
+        for (;;) {
+          phase_decide(c, s_lo, s_hi, n_lo, n_hi, tid, nthreads);
+          if (!grid_barrier(c, f)) return;
+          const uint32_t sc = vload(&c.ctl->split_count), nn = vload(&c.ctl->n_nodes);
+          if (sc == s_hi) break;
+          if (iters >= max_iters) {
+            if (tid == 0) set_error(c, E_ITER_CAP);
+            return;
+          }
+          s_lo = s_hi;
+          s_hi = sc;
+          n_lo = n_hi;
+          n_hi = nn;
+          ++iters;
+          phase_spill(c, s_lo, s_hi, blockIdx.x, gridDim.x);
+          if (!grid_barrier(c, f)) return;
+          const uint32_t n_spill = vload(&c.ctl->spill_count);
+          if (blockIdx.x == 0) phase_merge_pending(c);
+          phase_advance(c, bd.pts, bd.n, base, n_spill, warp0, nwarps);
+          if (!grid_barrier(c, f)) return;
+        }
+        const uint32_t n_spill = vload(&c.ctl->spill_count);
+        const uint32_t n_keys = min(vload(&c.ctl->nkeys), c.backlog_cap);
+        phase_store(c, bd.pts, bd.n, base, n_spill, n_keys, tid, nthreads);
+        if (!grid_barrier(c, f)) return;
+        if (tid == 0) phase_end(c, bd.n, iters);
+      }
+    }
+    if (tid == 0) {
+      f->consumed = b + 1;
+      if (budget_ns != NO_BUDGET && globaltimer_ns() - t_begin > budget_ns) f->stop = 1;
+    }
+    if (!grid_barrier(c, f)) return;
+  }
+}
+
+}  // namespace sl

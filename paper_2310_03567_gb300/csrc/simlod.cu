@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "device.cuh"
+#include "fused.cuh"
 #include "simlod.h"
 
 using namespace sl;
@@ -55,94 +56,24 @@ __global__ void __launch_bounds__(BLOCK) k_count1(Ctx c, const int4* pts, uint64
                (uint64_t)gridDim.x * warps_per_block);
 }
 
+// Decide / allocate; after the first count round of a rejected batch (no
+// thread changes the reject flag during this kernel) undo that round instead.
 __global__ void __launch_bounds__(BLOCK) k_decide(Ctx c, uint32_t s_lo, uint32_t s_hi,
                                                    uint32_t n_lo, uint32_t n_hi) {
-  phase_decide(c, s_lo, s_hi, n_lo, n_hi, blockIdx.x * (uint64_t)blockDim.x + threadIdx.x,
-               (uint64_t)gridDim.x * blockDim.x);
+  const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  if (*reinterpret_cast<volatile unsigned int*>(&c.ctl->reject)) {
+    phase_rollback(c, n_hi, t0, nt);
+    return;
+  }
+  phase_decide(c, s_lo, s_hi, n_lo, n_hi, t0, nt);
 }
 
-// One block per split leaf: zero its new grid, copy its stored points and
-// their gidx into its spill range, hand its chunks to the pending-free list.
 __global__ void __launch_bounds__(BLOCK) k_spill(Ctx c, uint32_t s_lo, uint32_t s_hi) {
-  constexpr uint32_t ROUND = 1024;
-  __shared__ uint32_t refs[ROUND];
-  __shared__ uint32_t s_nch, s_free0, s_n, s_bad;
-  for (uint32_t e = s_lo + blockIdx.x; e < s_hi; e += gridDim.x) {
-    const SplitEntry se = c.splits[e];
-    const uint32_t id = se.node;
-    NodeMeta& m = c.meta[id];
-    int4* g = reinterpret_cast<int4*>(grid_words(c, m.grid));
-    for (uint32_t q = threadIdx.x; q < c.grid_bytes / 16u; q += blockDim.x)
-      g[q] = make_int4(0, 0, 0, 0);
-    if (threadIdx.x == 0) {
-      s_bad = 0;
-      s_nch = m.n_chunks;
-      s_n = c.num[id];
-      s_free0 = atomicAdd(&c.ctl->pending_free, m.n_chunks);
-      if ((unsigned long long)s_free0 + m.n_chunks > c.max_chunks) set_error(c, E_POOL);
-    }
-    __syncthreads();
-    const uint32_t nch = s_nch, n = s_n, free0 = s_free0;
-    const bool ok = (unsigned long long)free0 + nch <= c.max_chunks;
-    uint32_t walk = m.head;  // used by thread 0 only
-    for (uint32_t r0 = 0; r0 < nch; r0 += ROUND) {
-      const uint32_t cnt = min(ROUND, nch - r0);
-      if (threadIdx.x == 0) {
-        for (uint32_t q = 0; q < cnt; ++q) {
-          if (!ref_ok(c, walk, c.chunk_bytes)) {  // list shorter than n_chunks
-            set_error(c, E_INTERNAL);
-            s_bad = 1;
-            break;
-          }
-          refs[q] = walk;
-          walk = *chunk_next(c, walk);
-        }
-      }
-      __syncthreads();
-      if (s_bad) break;
-      const uint64_t lo = (uint64_t)r0 * c.C;
-      const uint64_t hi = min((uint64_t)n, (uint64_t)(r0 + cnt) * c.C);
-      for (uint64_t idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
-        const uint32_t j = (uint32_t)(idx / c.C), q = (uint32_t)(idx - (uint64_t)j * c.C);
-        const uint32_t ref = refs[j - r0];
-        const uint64_t dst = se.spill_off + idx;
-        c.sp_pt[dst] = chunk_recs(c, ref)[q];
-        c.sp_gidx[dst] = chunk_aux(c, ref)[q];
-        c.sp_cur[dst] = id;
-      }
-      if (ok)
-        for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) c.pending[free0 + r0 + q] = refs[q];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      m.n_chunks = 0;
-      m.head = m.tail = NONE;
-      c.num[id] = 0;
-    }
-    __syncthreads();
-  }
+  phase_spill(c, s_lo, s_hi, blockIdx.x, gridDim.x);
 }
 
-// Move the chunks freed by this round's splits into the pool.
-__global__ void k_merge_pending(Ctx c) {
-  __shared__ int top;
-  __shared__ uint32_t np;
-  if (threadIdx.x == 0) {
-    top = c.ctl->pool_top;
-    np = c.ctl->pending_free;
-    if ((unsigned long long)top + np > c.max_chunks) {
-      set_error(c, E_POOL);
-      np = 0;
-    }
-  }
-  __syncthreads();
-  for (uint32_t q = threadIdx.x; q < np; q += blockDim.x) c.pool[top + q] = c.pending[q];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    c.ctl->pool_top = top + (int)np;
-    c.ctl->pending_free = 0;
-  }
-}
+__global__ void k_merge_pending(Ctx c) { phase_merge_pending(c); }
 
 __global__ void __launch_bounds__(BLOCK) k_advance(Ctx c, const int4* pts, uint64_t n,
                                                     unsigned long long base, uint32_t n_spill) {
@@ -158,49 +89,21 @@ __global__ void __launch_bounds__(BLOCK) k_store(Ctx c, const int4* pts, uint64_
               (uint64_t)gridDim.x * blockDim.x);
 }
 
-// Close an applied update: advance gidx, fold the update into the stats and
-// clear the per-update counters.
-__global__ void k_end(Ctx c, uint64_t n, uint32_t iters) {
-  Ctl* t = c.ctl;
-  const unsigned long long nk = min((unsigned long long)t->nkeys, (unsigned long long)c.backlog_cap);
-  t->base += n;
-  t->st_batches += 1;
-  t->st_points += n;
-  t->st_spilled += t->spill_count;
-  t->st_splits += t->split_count;
-  t->st_voxels += nk;
-  if (iters > t->st_iter_max) t->st_iter_max = iters;
-  t->st_rounds += iters;
-  t->last_points = n;
-  t->last_spilled = t->spill_count;
-  t->last_splits = t->split_count;
-  t->last_voxels = nk;
-  t->last_iters = iters;
-  t->spill_count = 0;
-  t->nkeys = 0;
-  t->alloc_seq = 0;
-  t->split_count = 0;
-}
+__global__ void k_end(Ctx c, uint64_t n, uint32_t iters) { phase_end(c, n, iters); }
 
-// Close a rejected update (the decide kernel already undid its counters).
-__global__ void k_end_rejected(Ctx c) {
-  Ctl* t = c.ctl;
-  t->reject = 0;
-  t->nkeys = 0;
-  t->st_rejected += 1;
-}
+__global__ void k_end_rejected(Ctx c) { phase_end_rejected(c); }
 
 }  // namespace
 
 // ================================================================ host side
 
-enum KernelId { K_COUNT = 0, K_DECIDE, K_SPILL, K_MERGE, K_ADVANCE, K_STORE, K_END, K_OTHER };
+enum KernelId { K_COUNT = 0, K_DECIDE, K_SPILL, K_MERGE, K_ADVANCE, K_STORE, K_END, K_FUSED };
 static const char* const kKernelNames[SIMLOD_N_KERNELS] = {
-    "count1", "decide", "spill", "merge_pending", "advance", "store", "end", "other"};
+    "count1", "decide", "spill", "merge_pending", "advance", "store", "end", "fused_update"};
 
 struct Layout {
-  size_t ctl, child, cnt, num, meta, pool, pending, alloc_refs, splits, sp_pt, sp_gidx, sp_cur,
-      sp_slot, b_cur, b_slot, hash, keys, staging, data, end;
+  size_t ctl, fctl, batches, child, cnt, num, meta, pool, pending, alloc_refs, splits, sp_pt,
+      sp_gidx, sp_cur, sp_slot, b_cur, b_slot, hash, keys, staging, data, end;
   uint64_t hash_slots, max_chunks, max_splits, data_bytes;
 };
 
@@ -216,6 +119,15 @@ struct simlod {
   int sticky;               // poison status
   cudaStream_t last_stream;
   int sm_count;
+  // fused form
+  int fused_grid;           // co-resident blocks of k_fused
+  bool mirror_stale;        // a fused launch ran since the last control-block read
+  unsigned long long rejected_async_seen;  // fused-launch rejections already reported
+  BatchDesc* desc_host;     // pinned staging of the batch table
+  cudaEvent_t desc_done;    // the last batch-table copy has finished
+  FusedCtl* fctl_host;      // pinned mirror of the fused control words
+  FusedCtl* fctl_dev;
+  BatchDesc* batches_dev;
   // timing
   bool timing;
   std::vector<cudaEvent_t> ev_pool;
@@ -277,6 +189,8 @@ bool plan_layout(const simlod_config* c, size_t arena_bytes, Layout* L) {
   L->max_splits = N / 8 + 1;
   L->hash_slots = next_pow2(2 * c->backlog_capacity);
   L->ctl = take(sizeof(Ctl));
+  L->fctl = take(sizeof(FusedCtl));
+  L->batches = take(sizeof(BatchDesc) * MAX_FUSED_BATCHES);
   L->child = take(4 * N);
   L->cnt = take(4 * N);
   L->num = take(4 * N);
@@ -313,6 +227,8 @@ void make_ctx(simlod_t* h) {
   const Layout& L = h->lay;
   uint8_t* a = h->arena;
   c.ctl = reinterpret_cast<Ctl*>(a + L.ctl);
+  h->fctl_dev = reinterpret_cast<FusedCtl*>(a + L.fctl);
+  h->batches_dev = reinterpret_cast<BatchDesc*>(a + L.batches);
   c.child = reinterpret_cast<uint32_t*>(a + L.child);
   c.cnt = reinterpret_cast<uint32_t*>(a + L.cnt);
   c.num = reinterpret_cast<uint32_t*>(a + L.num);
@@ -351,11 +267,13 @@ void make_ctx(simlod_t* h) {
 }
 
 int error_from_bits(uint32_t e) {
+  if (e & E_ITER_CAP) return SIMLOD_ERR_ITER_CAP;
   if (e & E_ARENA) return SIMLOD_ERR_ARENA_FULL;
   if (e & E_NODES) return SIMLOD_ERR_NODES_FULL;
   if (e & E_SPILL) return SIMLOD_ERR_SPILL_FULL;
   if (e & E_BACKLOG) return SIMLOD_ERR_BACKLOG_FULL;
   if (e & (E_ALLOC_REFS | E_POOL)) return SIMLOD_ERR_ARENA_FULL;
+  if (e & E_TIMEOUT) return SIMLOD_ERR_TIMEOUT;
   return SIMLOD_ERR_CUDA;
 }
 
@@ -421,10 +339,20 @@ int read_ctl(simlod_t* h, cudaStream_t s) {
     return SIMLOD_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return SIMLOD_ERR_CUDA;
   if (h->timing) harvest_timing(h);
+  if (h->mirror_stale) {
+    h->base = h->ctl_host->base;
+    h->n_nodes = h->ctl_host->n_nodes;
+    h->mirror_stale = false;
+  }
   return SIMLOD_OK;
 }
 
 int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
+  if (h->mirror_stale) {
+    int r0 = read_ctl(h, h->last_stream);
+    if (r0) return poison(h, r0);
+    if (h->ctl_host->error) return poison(h, error_from_bits(h->ctl_host->error));
+  }
   h->last_stream = s;
   const Ctx& c = h->ctx;
   const unsigned long long base = h->base;
@@ -441,7 +369,7 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
   const Ctl& t = *h->ctl_host;
   if (t.error) return poison(h, error_from_bits(t.error));
   if (t.reject) {
-    rc = launch(h, K_OTHER, s, [&] { k_end_rejected<<<1, 1, 0, s>>>(c); });
+    rc = launch(h, K_END, s, [&] { k_end_rejected<<<1, 1, 0, s>>>(c); });
     if (rc) return poison(h, rc);
     return SIMLOD_ERR_OUT_OF_BOUNDS;
   }
@@ -488,7 +416,61 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
   return SIMLOD_OK;
 }
 
-int init_octree(simlod_t* h, cudaStream_t s, bool clear_hash) {
+// Enqueue one fused launch over n batches (device pointers + counts).
+int launch_fused(simlod_t* h, const simlod_point* const* d_batches, const uint64_t* counts,
+                 uint32_t n, unsigned long long budget_ns, cudaStream_t s) {
+  if (h->fused_grid < 1) return SIMLOD_ERR_CUDA;
+  uint64_t total = 0;
+  for (uint32_t k = 0; k < n; ++k) {
+    if (counts[k] > h->cfg.max_batch_points) return SIMLOD_ERR_INVALID_ARG;
+    if (counts[k] && (!d_batches[k] || (reinterpret_cast<uintptr_t>(d_batches[k]) & 15u)))
+      return SIMLOD_ERR_INVALID_ARG;
+    total += counts[k];
+  }
+  if (h->base + total > (1ull << 32)) return SIMLOD_ERR_TOO_MANY_POINTS;
+  // the staging table may still feed the previous copy
+  if (cudaEventSynchronize(h->desc_done) != cudaSuccess) return poison(h, SIMLOD_ERR_CUDA);
+  for (uint32_t k = 0; k < n; ++k)
+    h->desc_host[k] = BatchDesc{reinterpret_cast<const int4*>(d_batches[k]), counts[k]};
+  h->last_stream = s;
+  if (cudaMemcpyAsync(h->batches_dev, h->desc_host, sizeof(BatchDesc) * n,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaEventRecord(h->desc_done, s) != cudaSuccess ||
+      cudaMemsetAsync(h->fctl_dev, 0, sizeof(FusedCtl), s) != cudaSuccess)
+    return poison(h, SIMLOD_ERR_CUDA);
+  Ctx c = h->ctx;
+  const BatchDesc* bt = h->batches_dev;
+  FusedCtl* f = h->fctl_dev;
+  uint32_t max_iters = h->cfg.max_expand_iters ? h->cfg.max_expand_iters : h->cfg.root_log2 + 1;
+  void* args[] = {&c, &bt, &n, &f, &budget_ns, &max_iters};
+  cudaError_t le = cudaSuccess;
+  int rc = launch(h, K_FUSED, s, [&] {
+    le = cudaLaunchCooperativeKernel((const void*)k_fused, dim3(h->fused_grid),
+                                     dim3(FUSED_BLOCK), args, 0, s);
+  });
+  if (rc || le != cudaSuccess) return poison(h, SIMLOD_ERR_CUDA);
+  h->base += total;  // upper bound until the next control-block read
+  h->mirror_stale = true;
+  return SIMLOD_OK;
+}
+
+// After a fused launch: wait, fold rejected batches into the status.
+int finish_fused(simlod_t* h, uint32_t* consumed) {
+  cudaStream_t s = h->last_stream;
+  if (cudaMemcpyAsync(h->fctl_host, h->fctl_dev, sizeof(FusedCtl), cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    return poison(h, SIMLOD_ERR_CUDA);
+  int rc = read_ctl(h, s);
+  if (rc) return poison(h, rc);
+  if (h->ctl_host->error) return poison(h, error_from_bits(h->ctl_host->error));
+  if (consumed) *consumed = h->fctl_host->consumed;
+  const unsigned long long rej = h->ctl_host->st_rejected_async;
+  const bool fresh = rej > h->rejected_async_seen;
+  h->rejected_async_seen = rej;
+  return fresh ? SIMLOD_ERR_OUT_OF_BOUNDS : SIMLOD_OK;
+}
+
+int init_octree(simlod_t* h, cudaStream_t s, bool clear_hash, bool wait) {
   const Ctx& c = h->ctx;
   if (clear_hash) {
     k_fill_hash<<<grid_for(h, h->lay.hash_slots, BLOCK), BLOCK, 0, s>>>(c.hash, h->lay.hash_slots);
@@ -496,10 +478,12 @@ int init_octree(simlod_t* h, cudaStream_t s, bool clear_hash) {
   }
   k_init<<<1, 1, 0, s>>>(c);
   if (cudaGetLastError() != cudaSuccess) return SIMLOD_ERR_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return SIMLOD_ERR_CUDA;
+  if (wait && cudaStreamSynchronize(s) != cudaSuccess) return SIMLOD_ERR_CUDA;
   h->base = 0;
   h->n_nodes = 1;
   h->sticky = 0;
+  h->rejected_async_seen = 0;
+  h->mirror_stale = false;
   h->last_stream = s;
   return SIMLOD_OK;
 }
@@ -560,10 +544,21 @@ SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t are
     return SIMLOD_ERR_CUDA;
   }
   memset(h->ctl_host, 0, sizeof(Ctl));
-  int rc = init_octree(h, static_cast<cudaStream_t>(stream), true);
+  int coop = 0, bpsm = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_fused, FUSED_BLOCK, 0) ==
+                  cudaSuccess)
+    h->fused_grid = std::min(bpsm, 4) * h->sm_count;
+  if (cudaMallocHost(reinterpret_cast<void**>(&h->desc_host),
+                     sizeof(BatchDesc) * MAX_FUSED_BATCHES) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&h->fctl_host), sizeof(FusedCtl)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->desc_done, cudaEventDisableTiming) != cudaSuccess) {
+    simlod_destroy(h);
+    return SIMLOD_ERR_CUDA;
+  }
+  int rc = init_octree(h, static_cast<cudaStream_t>(stream), true, true);
   if (rc) {
-    cudaFreeHost(h->ctl_host);
-    delete h;
+    simlod_destroy(h);
     return rc;
   }
   *out = h;
@@ -596,51 +591,44 @@ SIMLOD_API int simlod_insert_batch_host(simlod_t* h, const simlod_point* h_pts, 
   return insert_device(h, h->ctx.staging, n, s);
 }
 
+SIMLOD_API int simlod_insert_batches(simlod_t* h, const simlod_point* const* d_batches,
+                                     const uint64_t* counts, uint32_t n_batches, void* stream) {
+  if (!h || (n_batches && (!d_batches || !counts)) || n_batches > MAX_FUSED_BATCHES)
+    return SIMLOD_ERR_INVALID_ARG;
+  if (h->sticky) return SIMLOD_ERR_POISONED;
+  if (n_batches == 0) return SIMLOD_OK;
+  return launch_fused(h, d_batches, counts, n_batches, NO_BUDGET,
+                      static_cast<cudaStream_t>(stream));
+}
+
 SIMLOD_API int simlod_frame_update(simlod_t* h, const simlod_point* const* d_batches,
                                    const uint64_t* counts, uint32_t n_batches,
                                    uint64_t budget_ns, void* stream, uint32_t* consumed) {
-  if (!h || !consumed || (n_batches && (!d_batches || !counts))) return SIMLOD_ERR_INVALID_ARG;
+  if (!h || !consumed || (n_batches && (!d_batches || !counts)) ||
+      n_batches > MAX_FUSED_BATCHES)
+    return SIMLOD_ERR_INVALID_ARG;
   *consumed = 0;
   if (h->sticky) return SIMLOD_ERR_POISONED;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaEvent_t t0 = nullptr, t1 = nullptr;
-  if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess)
-    return SIMLOD_ERR_CUDA;
-  cudaEventRecord(t0, s);
-  int rc = SIMLOD_OK;
-  for (uint32_t k = 0; k < n_batches; ++k) {
-    if (k > 0) {
-      // Section 7.2: once the frame's budget is spent, stop and resume in the
-      // next frame; the check sits between batches.
-      cudaEventRecord(t1, s);
-      cudaEventSynchronize(t1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, t0, t1);
-      if ((double)ms * 1e6 > (double)budget_ns) break;
-    }
-    rc = simlod_insert_batch(h, d_batches[k], counts[k], stream);
-    if (rc) break;
-    *consumed = k + 1;
-  }
-  cudaEventDestroy(t0);
-  cudaEventDestroy(t1);
-  return rc;
+  if (n_batches == 0) return SIMLOD_OK;
+  const unsigned long long budget = budget_ns >= NO_BUDGET ? NO_BUDGET - 1 : budget_ns;
+  int rc = launch_fused(h, d_batches, counts, n_batches, budget, static_cast<cudaStream_t>(stream));
+  if (rc) return rc;
+  return finish_fused(h, consumed);
 }
 
 SIMLOD_API int simlod_reset(simlod_t* h, void* stream) {
   if (!h) return SIMLOD_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // a poisoned update may have left claims in the table
-  return init_octree(h, s, h->sticky != 0);
+  const bool dirty = h->sticky != 0;
+  if (dirty) cudaStreamSynchronize(h->last_stream);
+  return init_octree(h, s, dirty, dirty);
 }
 
 SIMLOD_API int simlod_sync(simlod_t* h) {
   if (!h) return SIMLOD_ERR_INVALID_ARG;
   if (h->sticky) return SIMLOD_ERR_POISONED;
-  int rc = read_ctl(h, h->last_stream);
-  if (rc) return poison(h, rc);
-  if (h->ctl_host->error) return poison(h, error_from_bits(h->ctl_host->error));
-  return SIMLOD_OK;
+  return finish_fused(h, nullptr);
 }
 
 SIMLOD_API int simlod_get_stats(simlod_t* h, simlod_stats* out) {
@@ -802,6 +790,9 @@ SIMLOD_API int simlod_destroy(simlod_t* h) {
   harvest_timing(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
+  if (h->desc_host) cudaFreeHost(h->desc_host);
+  if (h->fctl_host) cudaFreeHost(h->fctl_host);
+  if (h->desc_done) cudaEventDestroy(h->desc_done);
   delete h;
   return SIMLOD_OK;
 }

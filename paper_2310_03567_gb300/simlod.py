@@ -99,6 +99,7 @@ SIGNATURES = {
     "simlod_create": (_I32, [ctypes.POINTER(Config), _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
     "simlod_insert_batch": (_I32, [_P, _P, _U64, _P]),
     "simlod_insert_batch_host": (_I32, [_P, _P, _U64, _P]),
+    "simlod_insert_batches": (_I32, [_P, _P, _P, _U32, _P]),
     "simlod_frame_update": (_I32, [_P, _P, _P, _U32, _U64, _P, ctypes.POINTER(_U32)]),
     "simlod_reset": (_I32, [_P, _P]),
     "simlod_sync": (_I32, [_P]),
@@ -267,6 +268,31 @@ class Octree:
             self._h, ptrs, counts, n, budget_ns,
             _stream_ptr(stream if stream is not None else self.stream), ctypes.byref(consumed))
         return rc, int(consumed.value)
+
+    def insert_many(self, batches, stream=None, check: bool = True) -> int:
+        """Fused form: one persistent launch over a list of CUDA tensors
+        (asynchronous; errors and rejections surface at sync())."""
+        n = len(batches)
+        s = None
+        for b in batches:
+            s = self._order(stream, b)
+        if s is None:
+            s = stream if stream is not None else self.stream
+        ptrs = (ctypes.c_void_p * max(n, 1))(*[b.data_ptr() for b in batches])
+        counts = (ctypes.c_uint64 * max(n, 1))(
+            *[b.numel() * b.element_size() // 16 for b in batches])
+        rc = self._lib.simlod_insert_batches(self._h, ptrs, counts, n, _stream_ptr(s))
+        if check and rc != OK:
+            raise SimlodError(rc, "simlod_insert_batches")
+        return rc
+
+    def insert_many_ptrs(self, ptrs, counts, stream=None) -> int:
+        """Fused form over raw device pointers (no stream ordering done here)."""
+        n = len(ptrs)
+        p = (ctypes.c_void_p * max(n, 1))(*ptrs)
+        c = (ctypes.c_uint64 * max(n, 1))(*counts)
+        return self._lib.simlod_insert_batches(
+            self._h, p, c, n, _stream_ptr(stream if stream is not None else self.stream))
 
     def reset(self, stream=None):
         rc = self._lib.simlod_reset(self._h, _stream_ptr(stream if stream is not None else self.stream))
