@@ -219,7 +219,7 @@ def run_ours(args):
                                 max_batch_points=max_batch,
                                 spill_capacity=max(8 << 20, 2 * max_batch),
                                 max_nodes=1 << 21)
-    data_bytes = max(4 << 30, n_points * 80)
+    data_bytes = max(256 << 20, n_points * 80)
     arena = simlod.make_arena(cfg, data_bytes)
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
@@ -289,12 +289,17 @@ def run_ours(args):
     lat_plain = []
     pe0 = torch.cuda.Event(enable_timing=True)
     pe1 = torch.cuda.Event(enable_timing=True)
+    plain_pass()  # warm
+    check(tree.sync(), "plain warm-up")
+    tree.set_timing(True, clear=True)
     pe0.record(stream)
     plain_pass(lat_plain)
     pe1.record(stream)
     torch.cuda.synchronize()
+    tree.set_timing(False)
     check(tree.sync(), "plain pass")
     plain_ms = pe0.elapsed_time(pe1)
+    plain_k = {k: v[1] for k, v in tree.timing().items() if v[0]}
     lat_f = [a.elapsed_time(b) for a, b in lat_fused]
     lat_p = [a.elapsed_time(b) for a, b in lat_plain]
 
@@ -347,7 +352,7 @@ def run_ours(args):
                        "plain_p50": percentile(lat_p, 50), "plain_p99": percentile(lat_p, 99),
                        "batches": len(lat_f)},
         "plain": {"value": n_points / (plain_ms * 1e-3) / 1e6, "unit": UNIT,
-                  "ms_per_step": plain_ms},
+                  "ms_per_step": plain_ms, "kernels_ms_per_step": plain_k},
         "roofline": {"bound": "hbm", "kernel": "k_fused", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                      "alg_bytes_per_launch": upd_bytes, "peak_source": peak_src},

@@ -1,7 +1,7 @@
 // Device-side data layout and the phase functions of one octree update.
 //
 // The update of one batch follows Section 5 of the paper, re-planned for a
-// GPU that can hold the whole per-update working set in L2:
+// GPU that can keep the per-update working set in L2:
 //
 //  count1  every batch point walks from the root to its leaf. At every inner
 //          node on the way it tests the node's occupancy bit (Section 3.3);
@@ -10,25 +10,30 @@
 //          "Counting"); the ticket is its final slot if the leaf does not
 //          split. The leaf and ticket are kept per point (the cursor).
 //  decide  per candidate node: a leaf whose stored + counted points exceed T
-//          splits (Section 5.1, "Splitting"): 8 children, a zeroed grid, its
-//          points reserved in the spill buffer. Any other counted node is
-//          final and gets its chunks now (Section 5.3).
-//  spill   per split leaf: copy its stored points (with gidx) to the spill
-//          buffer, zero its grid, free its chunks (Section 3.4).
-//  advance points whose cursor leaf split (batch or spill) sample that
-//          node's fresh grid and move one level down, counting into the
-//          child. Repeated with decide/spill until nothing splits: the
-//          paper's iterative deepening, but each round touches only the
-//          points that have to move.
+//          splits (Section 5.1, "Splitting"): 8 children, a grid, and one
+//          spill task per chunk of its stored points. Any other counted node
+//          is final and gets its chunks now (Section 5.3).
+//  advance points whose cursor node split in the previous round (batch
+//          points, and the stored points of split leaves, read in place from
+//          their old chunks through the spill tasks) sample that node's grid
+//          and move one level down, counting into the child; the grids of
+//          the previous round's splits are zeroed alongside. Repeated with
+//          decide until nothing splits: the paper's iterative deepening, but
+//          each round touches only the points that have to move.
 //  store   every point goes to its cursor leaf at its ticket slot; every new
 //          voxel goes to its node (Section 5.4); occupancy bits are set here,
-//          after all claims of the update were made.
+//          after all claims of the update; the chunks of split leaves return
+//          to the pool (Section 3.4), now that their points were re-stored.
 //
 // Voxel claims: the paper lets the first point that finds an empty cell win.
 // Here all contenders of an update for a (node, cell) meet in an open-
 // addressing table with a 64-bit atomicMin on (gidx << 32 | rgba), so the
 // lowest arrival index wins regardless of thread timing. The table entries of
 // an update are listed (the backlog of Section 5.2) and cleared by store.
+//
+// Descents read the node table (first child, grid reference) from a copy in
+// shared memory of the first NODE_CACHE nodes, taken at the start of each
+// count / advance pass; the node ids of the upper levels are the smallest.
 #pragma once
 
 #include <cstdint>
@@ -41,8 +46,12 @@ constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr unsigned long long HASH_EMPTY = ~0ull;
 constexpr uint32_t FULL_MASK = 0xFFFFFFFFu;
 constexpr int MAX_PROBES = 1 << 14;
-constexpr uint32_t REF_BYTES = 256;  // chunk and grid references count 256-byte units
+constexpr uint32_t REF_BYTES = 256;  // chunk, grid and directory references count 256-byte units
 constexpr uint32_t CHUNK_HEADER = 16;
+constexpr uint32_t NODE_CACHE = 12288;                 // nodes mirrored in shared memory
+constexpr uint32_t NODE_CACHE_BYTES = NODE_CACHE * 8;  // child + grid reference
+constexpr uint32_t TASK_PART = 128;                    // points of a spill task per warp unit
+constexpr uint32_t ZERO_UNIT = 4096;                   // bytes of grid zeroed per warp unit
 
 // Sticky device error bits.
 enum : uint32_t {
@@ -66,11 +75,11 @@ struct Ctl {
   int pool_top;                      // chunk refs in the pool
   unsigned int error;                // sticky E_* bits
   unsigned int reject;               // out-of-cube point seen in this update
-  unsigned int spill_count;          // spill entries of this update
+  unsigned int spill_count;          // re-inserted points of this update
   unsigned int nkeys;                // new voxels (backlog entries) of this update
   unsigned int alloc_seq;            // alloc_refs entries of this update
   unsigned int split_count;          // split-list entries of this update
-  unsigned int pending_free;         // freed chunk refs waiting for the pool
+  unsigned int ntasks;               // spill tasks (= freed chunks) of this update
   unsigned int pad0;
   unsigned long long st_batches, st_points, st_rejected, st_spilled, st_splits, st_voxels,
       st_iter_max, st_rounds;
@@ -86,7 +95,7 @@ struct NodeMeta {
   uint32_t level;
   uint32_t n_chunks;
   uint32_t head, tail;  // chunk list (points of a leaf, voxels of an inner node)
-  uint32_t grid;        // occupancy grid ref, NONE for leaves
+  uint32_t dir;         // chunk directory of a leaf (ref), NONE if none
   uint32_t st_nch;      // store map of the current update: chunks before allocation,
   uint32_t st_tail;     //   the tail before allocation,
   uint32_t st_seq;      //   first alloc_refs entry of the newly allocated chunks
@@ -104,20 +113,29 @@ struct SplitEntry {
   uint32_t spill_off;
 };
 
+// The stored points of one chunk of a split leaf, re-inserted this update:
+// point q of the chunk is spill entry dst + q.
+struct SpillTask {
+  uint32_t ref;   // the chunk
+  uint32_t node;  // the leaf that split
+  uint32_t dst;   // first spill entry
+  uint32_t n;     // points in the chunk
+};
+
 // Everything a phase needs: arena pointers and the configuration.
 struct Ctx {
   Ctl* ctl;
-  uint32_t* child;  // first child id or NONE (leaf), per node
-  uint32_t* cnt;    // per-update counter: new points (leaf) or new voxels (inner)
-  uint32_t* num;    // stored points (leaf) or voxels (inner)
+  uint32_t* child;    // first child id or NONE (leaf), per node
+  uint32_t* gridref;  // occupancy grid ref or NONE, per node
+  uint32_t* cnt;      // per-update counter: new points (leaf) or new voxels (inner)
+  uint32_t* num;      // stored points (leaf) or voxels (inner)
   NodeMeta* meta;
   uint32_t* pool;
-  uint32_t* pending;
+  uint32_t* pending;  // chunk refs freed by this update's splits (one per task)
   uint32_t* alloc_refs;
   SplitEntry* splits;
-  int4* sp_pt;
-  uint32_t* sp_gidx;
-  uint32_t* sp_cur;
+  SpillTask* tasks;
+  uint32_t* sp_cur;   // per spill entry: cursor node and slot (after its first move)
   uint32_t* sp_slot;
   uint32_t* b_cur;
   uint32_t* b_slot;
@@ -128,7 +146,7 @@ struct Ctx {
   int4* staging;
   int32_t rmin[3];
   uint32_t rlog2, T, C, G;
-  uint32_t chunk_bytes, chunk_units, grid_bytes;
+  uint32_t chunk_bytes, chunk_units, grid_bytes, dir_bytes, dir_cap;
   uint32_t hash_mask;
   uint32_t max_nodes, max_chunks, spill_cap, backlog_cap, max_splits;
   uint64_t max_batch;
@@ -151,20 +169,20 @@ __device__ __forceinline__ void set_error(const Ctx& c, uint32_t bits) {
   atomicOr(&c.ctl->error, bits);
 }
 
-__device__ __forceinline__ uint8_t* chunk_ptr(const Ctx& c, uint32_t ref) {
+__device__ __forceinline__ uint8_t* ref_ptr(const Ctx& c, uint32_t ref) {
   return c.data + (size_t)ref * REF_BYTES;
 }
 
 __device__ __forceinline__ uint32_t* chunk_next(const Ctx& c, uint32_t ref) {
-  return reinterpret_cast<uint32_t*>(chunk_ptr(c, ref));
+  return reinterpret_cast<uint32_t*>(ref_ptr(c, ref));
 }
 
 __device__ __forceinline__ int4* chunk_recs(const Ctx& c, uint32_t ref) {
-  return reinterpret_cast<int4*>(chunk_ptr(c, ref) + CHUNK_HEADER);
+  return reinterpret_cast<int4*>(ref_ptr(c, ref) + CHUNK_HEADER);
 }
 
 __device__ __forceinline__ uint32_t* chunk_aux(const Ctx& c, uint32_t ref) {
-  return reinterpret_cast<uint32_t*>(chunk_ptr(c, ref) + CHUNK_HEADER + 16u * c.C);
+  return reinterpret_cast<uint32_t*>(ref_ptr(c, ref) + CHUNK_HEADER + 16u * c.C);
 }
 
 // A reference that stays inside the data region for `bytes` bytes.
@@ -173,7 +191,11 @@ __device__ __forceinline__ bool ref_ok(const Ctx& c, uint32_t ref, uint32_t byte
 }
 
 __device__ __forceinline__ uint32_t* grid_words(const Ctx& c, uint32_t ref) {
-  return reinterpret_cast<uint32_t*>(c.data + (size_t)ref * REF_BYTES);
+  return reinterpret_cast<uint32_t*>(ref_ptr(c, ref));
+}
+
+__device__ __forceinline__ uint32_t* dir_entries(const Ctx& c, uint32_t ref) {
+  return reinterpret_cast<uint32_t*>(ref_ptr(c, ref));
 }
 
 // Coordinates relative to the root minimum; false when outside the root cube.
@@ -206,6 +228,38 @@ __device__ __forceinline__ uint32_t cell_axis(uint32_t r, uint32_t L, uint32_t G
 __device__ __forceinline__ uint32_t cell_index(uint32_t rx, uint32_t ry, uint32_t rz, uint32_t L,
                                                uint32_t G) {
   return cell_axis(rx, L, G) | (cell_axis(ry, L, G) << G) | (cell_axis(rz, L, G) << (2u * G));
+}
+
+// ------------------------------------------------------- node-table cache
+
+// Shared-memory copy of child[] and gridref[] for nodes [0, NODE_CACHE).
+struct NodeCache {
+  uint32_t* child;
+  uint32_t* grid;
+  uint32_t n;  // cached nodes
+};
+
+// The whole block loads the cache (call after a grid/kernel boundary).
+__device__ __forceinline__ NodeCache load_node_cache(const Ctx& c, uint32_t* smem,
+                                                     uint32_t n_nodes) {
+  NodeCache nc;
+  nc.child = smem;
+  nc.grid = smem + NODE_CACHE;
+  nc.n = n_nodes < NODE_CACHE ? n_nodes : NODE_CACHE;
+  for (uint32_t i = threadIdx.x; i < nc.n; i += blockDim.x) {
+    nc.child[i] = c.child[i];
+    nc.grid[i] = c.gridref[i];
+  }
+  __syncthreads();
+  return nc;
+}
+
+__device__ __forceinline__ uint32_t node_child(const Ctx& c, NodeCache nc, uint32_t id) {
+  return id < nc.n ? nc.child[id] : c.child[id];
+}
+
+__device__ __forceinline__ uint32_t node_grid(const Ctx& c, NodeCache nc, uint32_t id) {
+  return id < nc.n ? nc.grid[id] : c.gridref[id];
 }
 
 // -------------------------------------------------------- voxel claims
@@ -292,9 +346,12 @@ __device__ __forceinline__ uint32_t warp_count(const Ctx& c, bool valid, uint32_
 
 // ------------------------------------------------------------ phase: count1
 
-// Iteration 1 for the batch points [0, n): descend, claim, count.
-__device__ void phase_count1(const Ctx& c, const int4* pts, uint64_t n, unsigned long long base,
-                             uint64_t warp0, uint64_t nwarps) {
+// Iteration 1 for the batch points [0, n): descend, claim, count. `smem`
+// holds NODE_CACHE_BYTES of dynamic shared memory; n_nodes is the node count.
+__device__ void phase_count1(const Ctx& c, uint32_t* smem, uint32_t n_nodes, const int4* pts,
+                             uint64_t n, unsigned long long base, uint64_t warp0,
+                             uint64_t nwarps) {
+  const NodeCache nc = load_node_cache(c, smem, n_nodes);
   const uint32_t lane = lane_id();
   for (uint64_t w = warp0; w * 32 < n; w += nwarps) {
     uint64_t i = w * 32 + lane;
@@ -312,12 +369,12 @@ __device__ void phase_count1(const Ctx& c, const int4* pts, uint64_t n, unsigned
       bool inner = false, want = false;
       uint32_t cell = 0, nxt = 0;
       if (walking) {
-        uint32_t ch = c.child[node];
+        const uint32_t ch = node_child(c, nc, node);
         if (ch == NONE) {
           walking = false;
         } else {
           cell = cell_index(rx, ry, rz, L, c.G);
-          const uint32_t gref = c.meta[node].grid;
+          const uint32_t gref = node_grid(c, nc, node);
           nxt = ch + octant(rx, ry, rz, L);
           if (!ref_ok(c, gref, c.grid_bytes) || nxt >= c.max_nodes) {
             set_error(c, E_INTERNAL);
@@ -346,15 +403,17 @@ __device__ void phase_count1(const Ctx& c, const int4* pts, uint64_t n, unsigned
 
 // ----------------------------------------------------------- phase: advance
 
-// Later iterations: items whose cursor node split in the previous round
-// sample that node's fresh grid and count into the child below. Returns true
-// when the item moved; its new cursor and slot are then in cur and slot.
-__device__ __forceinline__ bool advance_item(const Ctx& c, bool valid, int4 p, uint32_t gidx,
-                                             uint32_t& cur, uint32_t& slot) {
+// One item whose cursor node may have split in the previous round: if so it
+// samples that node's grid (empty until store, so every point contends) and
+// moves one level down, counting into the child. Returns true when it moved;
+// cur and slot then hold the new cursor and slot.
+__device__ __forceinline__ bool advance_item(const Ctx& c, NodeCache nc, bool valid,
+                                             int4 p, uint32_t gidx, uint32_t& cur,
+                                             uint32_t& slot) {
   const uint32_t node = cur;
   const bool in_range = node < c.max_nodes;
   if (valid && !in_range) set_error(c, E_INTERNAL);
-  const uint32_t ch = (valid && in_range) ? c.child[node] : NONE;
+  const uint32_t ch = (valid && in_range) ? node_child(c, nc, node) : NONE;
   const bool moving = valid && ch != NONE && ch + 8u <= c.max_nodes;
   uint32_t rx = 0, ry = 0, rz = 0, L = 0, cell = 0, nxt = 0;
   if (moving) {
@@ -363,7 +422,6 @@ __device__ __forceinline__ bool advance_item(const Ctx& c, bool valid, int4 p, u
     cell = cell_index(rx, ry, rz, L, c.G);
     nxt = ch + octant(rx, ry, rz, L);
   }
-  // the grid of a node split in this update is empty until store
   warp_claim(c, moving, ((unsigned long long)node << (3u * c.G)) | cell, gidx, (uint32_t)p.w,
              node);
   const uint32_t s = warp_count(c, moving, nxt);
@@ -374,29 +432,67 @@ __device__ __forceinline__ bool advance_item(const Ctx& c, bool valid, int4 p, u
   return moving;
 }
 
-__device__ void phase_advance(const Ctx& c, const int4* pts, uint64_t n, unsigned long long base,
-                              uint32_t n_spill, uint64_t warp0, uint64_t nwarps) {
+// Round of the expansion after the first: the batch points, then the spill
+// tasks [0, t_hi) (tasks [t_lo, t_hi) are new: their points still sit at the
+// split leaf), and zeroing the grids of the splits [s_lo, s_hi) of the
+// previous round. Work is cut into warp units so that all warps share it.
+__device__ void phase_advance(const Ctx& c, uint32_t* smem, uint32_t n_nodes, const int4* pts,
+                              uint64_t n, unsigned long long base, uint32_t t_lo, uint32_t t_hi,
+                              uint32_t s_lo, uint32_t s_hi, uint64_t warp0, uint64_t nwarps) {
+  const NodeCache nc = load_node_cache(c, smem, n_nodes);
   const uint32_t lane = lane_id();
-  const uint64_t wb = (n + 31) / 32, ws = (n_spill + 31ull) / 32;
-  for (uint64_t w = warp0; w < wb + ws; w += nwarps) {
-    if (w < wb) {
-      const uint64_t i = w * 32 + lane;
+  const uint32_t zpg = (c.grid_bytes + ZERO_UNIT - 1) / ZERO_UNIT;  // zero units per grid
+  const uint32_t parts = (c.C + TASK_PART - 1) / TASK_PART;       // units per task
+  const uint64_t uz = (uint64_t)(s_hi - s_lo) * zpg;
+  const uint64_t ub = (n + 31) / 32;
+  const uint64_t ut = (uint64_t)t_hi * parts;
+  for (uint64_t w = warp0; w < uz + ub + ut; w += nwarps) {
+    if (w < uz) {
+      const uint32_t id = c.splits[s_lo + (uint32_t)(w / zpg)].node;
+      const uint32_t gref = id < c.max_nodes ? c.gridref[id] : NONE;
+      if (!ref_ok(c, gref, c.grid_bytes)) {
+        if (lane == 0) set_error(c, E_INTERNAL);
+        continue;
+      }
+      const uint32_t lo = (uint32_t)(w % zpg) * ZERO_UNIT;
+      const uint32_t hi = min(lo + ZERO_UNIT, c.grid_bytes);
+      int4* g = reinterpret_cast<int4*>(grid_words(c, gref));
+      for (uint32_t b = lo / 16 + lane; b < hi / 16; b += 32) g[b] = make_int4(0, 0, 0, 0);
+    } else if (w < uz + ub) {
+      const uint64_t i = (w - uz) * 32 + lane;
       const bool valid = i < n;
       const int4 p = valid ? __ldg(pts + i) : make_int4(0, 0, 0, 0);
       uint32_t cur = valid ? c.b_cur[i] : 0u, slot = 0;
-      if (advance_item(c, valid, p, (uint32_t)(base + i), cur, slot)) {
+      if (advance_item(c, nc, valid, p, (uint32_t)(base + i), cur, slot)) {
         c.b_cur[i] = cur;
         c.b_slot[i] = slot;
       }
     } else {
-      const uint64_t e = (w - wb) * 32 + lane;
-      const bool valid = e < n_spill;
-      const int4 p = valid ? c.sp_pt[e] : make_int4(0, 0, 0, 0);
-      const uint32_t g = valid ? c.sp_gidx[e] : 0u;
-      uint32_t cur = valid ? c.sp_cur[e] : 0u, slot = 0;
-      if (advance_item(c, valid, p, g, cur, slot)) {
-        c.sp_cur[e] = cur;
-        c.sp_slot[e] = slot;
+      const uint64_t u = w - uz - ub;
+      const uint32_t t = (uint32_t)(u / parts), part = (uint32_t)(u % parts);
+      const SpillTask tk = c.tasks[t];
+      const bool task_ok = ref_ok(c, tk.ref, c.chunk_bytes) && tk.n <= c.C &&
+                           (unsigned long long)tk.dst + tk.n <= c.spill_cap;
+      if (!task_ok) {
+        if (lane == 0) set_error(c, E_INTERNAL);
+        continue;
+      }
+      const bool fresh = t >= t_lo;
+      const uint32_t q_end = min(tk.n, (part + 1) * TASK_PART);
+      for (uint32_t q0 = part * TASK_PART; q0 < q_end; q0 += 32) {
+        const uint32_t q = q0 + lane;
+        const bool valid = q < q_end;
+        const uint32_t e = tk.dst + q;
+        uint32_t cur = valid ? (fresh ? tk.node : c.sp_cur[e]) : 0u, slot = 0;
+        // read the point only when its cursor node split (it moves)
+        const uint32_t ch = (valid && cur < c.max_nodes) ? node_child(c, nc, cur) : NONE;
+        const bool may_move = ch != NONE;
+        const int4 p = may_move ? chunk_recs(c, tk.ref)[q] : make_int4(0, 0, 0, 0);
+        const uint32_t g = may_move ? chunk_aux(c, tk.ref)[q] : 0u;
+        if (advance_item(c, nc, valid, p, g, cur, slot)) {
+          c.sp_cur[e] = cur;
+          c.sp_slot[e] = slot;
+        }
       }
     }
   }
@@ -421,8 +517,9 @@ __device__ __forceinline__ uint32_t pool_take(const Ctx& c, uint32_t k, int* fir
 }
 
 // Section 5.3: give node `id` ceil(total / C) chunks, pool first, then the
-// bump allocator; link them and record the store map for this update.
-__device__ void alloc_chunks(const Ctx& c, uint32_t id, uint32_t total) {
+// bump allocator; link them, note them in a leaf's directory and record the
+// store map for this update.
+__device__ void alloc_chunks(const Ctx& c, uint32_t id, uint32_t total, bool leaf) {
   NodeMeta& m = c.meta[id];
   const uint32_t have = m.n_chunks;
   const uint32_t need = (uint32_t)(((unsigned long long)total + c.C - 1) / c.C);
@@ -449,6 +546,7 @@ __device__ void alloc_chunks(const Ctx& c, uint32_t id, uint32_t total) {
     }
     atomicAdd(&c.ctl->chunks_bumped, (unsigned long long)rest);
   }
+  uint32_t* dir = (leaf && ref_ok(c, m.dir, c.dir_bytes)) ? dir_entries(c, m.dir) : nullptr;
   uint32_t prev = m.tail;
   for (uint32_t q = 0; q < k; ++q) {
     uint32_t ref = q < from_pool ? c.pool[pfirst + (int)q]
@@ -457,17 +555,27 @@ __device__ void alloc_chunks(const Ctx& c, uint32_t id, uint32_t total) {
     *chunk_next(c, ref) = NONE;
     if (prev == NONE) m.head = ref;
     else *chunk_next(c, prev) = ref;
+    if (dir && have + q < c.dir_cap) dir[have + q] = ref;
     prev = ref;
   }
   m.tail = prev;
   m.n_chunks = need;
 }
 
-// Section 5.1: split leaf `id` whose count exceeds T.
+// Section 5.1: split leaf `id` whose count exceeds T: 8 children (with chunk
+// directories), a grid for the node (zeroed in the next round), and one spill
+// task per chunk of its stored points; those chunks return to the pool at the
+// end of the update.
 __device__ void split_leaf(const Ctx& c, uint32_t id) {
   const uint32_t c0 = atomicAdd(&c.ctl->n_nodes, 8u);
   if ((unsigned long long)c0 + 8 > c.max_nodes) {
     set_error(c, E_NODES);
+    return;
+  }
+  const unsigned long long dbase = atomicAdd(&c.ctl->bump, 8ull * c.dir_bytes);
+  const unsigned long long g = atomicAdd(&c.ctl->bump, (unsigned long long)c.grid_bytes);
+  if (dbase + 8ull * c.dir_bytes > c.data_bytes || g + c.grid_bytes > c.data_bytes) {
+    set_error(c, E_ARENA);
     return;
   }
   NodeMeta& m = c.meta[id];
@@ -480,27 +588,36 @@ __device__ void split_leaf(const Ctx& c, uint32_t id) {
     cm.level = m.level + 1u;
     cm.n_chunks = 0;
     cm.head = cm.tail = NONE;
-    cm.grid = NONE;
+    cm.dir = (uint32_t)((dbase + (unsigned long long)k * c.dir_bytes) / REF_BYTES);
     cm.st_nch = 0;
     cm.st_tail = NONE;
     cm.st_seq = 0;
     for (int q = 0; q < 5; ++q) cm.pad[q] = 0;
     c.meta[c0 + k] = cm;
     c.child[c0 + k] = NONE;
+    c.gridref[c0 + k] = NONE;
     c.cnt[c0 + k] = 0;
     c.num[c0 + k] = 0;
   }
-  const unsigned long long g = atomicAdd(&c.ctl->bump, (unsigned long long)c.grid_bytes);
-  if (g + c.grid_bytes > c.data_bytes) {
-    set_error(c, E_ARENA);
-    return;
-  }
-  m.grid = (uint32_t)(g / REF_BYTES);
   const uint32_t stored = c.num[id];
+  const uint32_t nch = m.n_chunks;
   const uint32_t s0 = atomicAdd(&c.ctl->spill_count, stored);
+  const uint32_t t0 = atomicAdd(&c.ctl->ntasks, nch);
   if ((unsigned long long)s0 + stored > c.spill_cap) {
     set_error(c, E_SPILL);
     return;
+  }
+  if ((unsigned long long)t0 + nch > c.max_chunks || nch > c.dir_cap ||
+      (nch && !ref_ok(c, m.dir, c.dir_bytes))) {
+    set_error(c, E_INTERNAL);
+    return;
+  }
+  const uint32_t* dir = nch ? dir_entries(c, m.dir) : nullptr;
+  for (uint32_t j = 0; j < nch; ++j) {
+    const uint32_t ref = dir[j];
+    const uint32_t first = j * c.C;
+    c.tasks[t0 + j] = SpillTask{ref, id, s0 + first, min(c.C, stored - first)};
+    c.pending[t0 + j] = ref;
   }
   const uint32_t e = atomicAdd(&c.ctl->split_count, 1u);
   if (e >= c.max_splits) {
@@ -508,6 +625,11 @@ __device__ void split_leaf(const Ctx& c, uint32_t id) {
     return;
   }
   c.splits[e] = SplitEntry{id, s0};
+  c.gridref[id] = (uint32_t)(g / REF_BYTES);
+  m.n_chunks = 0;
+  m.head = m.tail = NONE;
+  m.dir = NONE;
+  c.num[id] = 0;
   c.cnt[id] = 0;
   c.child[id] = c0;
 }
@@ -522,10 +644,10 @@ __device__ __forceinline__ void decide_node(const Ctx& c, uint32_t id) {
       split_leaf(c, id);
       return;
     }
-    alloc_chunks(c, id, total);
+    alloc_chunks(c, id, total, true);
     c.num[id] = total;
   } else {
-    alloc_chunks(c, id, c.num[id] + k);
+    alloc_chunks(c, id, c.num[id] + k, false);
     c.num[id] += k;
   }
   c.cnt[id] = 0;
@@ -579,19 +701,34 @@ __device__ __forceinline__ void store_rec(const Ctx& c, uint32_t node, uint32_t 
   chunk_aux(c, ref)[q] = aux;
 }
 
+// Store the batch points, the re-inserted points of the spill tasks [0,
+// n_tasks) and the n_keys new voxels; hand the chunks of split leaves (one
+// per task) to the pool above pool_top (the caller then raises pool_top).
 __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned long long base,
-                            uint32_t n_spill, uint32_t n_keys, uint64_t t0, uint64_t nthreads) {
+                            uint32_t n_tasks, uint32_t n_keys, int pool_top, uint64_t t0,
+                            uint64_t nthreads) {
   for (uint64_t i = t0; i < n; i += nthreads)
     store_rec(c, c.b_cur[i], c.b_slot[i], __ldg(pts + i), (uint32_t)(base + i));
-  for (uint64_t e = t0; e < n_spill; e += nthreads)
-    store_rec(c, c.sp_cur[e], c.sp_slot[e], c.sp_pt[e], c.sp_gidx[e]);
+  const uint64_t tp = (uint64_t)n_tasks * c.C;
+  for (uint64_t u = t0; u < tp; u += nthreads) {
+    const uint32_t t = (uint32_t)(u / c.C), q = (uint32_t)(u - (uint64_t)t * c.C);
+    const SpillTask tk = c.tasks[t];
+    if (q >= tk.n) continue;
+    if (!ref_ok(c, tk.ref, c.chunk_bytes) || (unsigned long long)tk.dst + tk.n > c.spill_cap) {
+      set_error(c, E_INTERNAL);
+      continue;
+    }
+    const uint32_t e = tk.dst + q;
+    store_rec(c, c.sp_cur[e], c.sp_slot[e], chunk_recs(c, tk.ref)[q], chunk_aux(c, tk.ref)[q]);
+  }
   const uint32_t G = c.G, cmask = (1u << (3u * G)) - 1u, amask = (1u << G) - 1u;
   for (uint64_t e = t0; e < n_keys; e += nthreads) {
     const uint2 k = c.keys[e];
     HSlot* s = c.hash + k.x;
     const unsigned long long key = s->key, val = s->val;
     const uint32_t node = (uint32_t)(key >> (3u * G)), cell = (uint32_t)key & cmask;
-    if (node >= c.max_nodes || !ref_ok(c, c.meta[node].grid, c.grid_bytes)) {
+    const uint32_t gref = node < c.max_nodes ? c.gridref[node] : NONE;
+    if (!ref_ok(c, gref, c.grid_bytes)) {
       set_error(c, E_INTERNAL);
       continue;
     }
@@ -605,112 +742,26 @@ __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned 
     v.z = m.min[2] + (int32_t)(((2ull * cz + 1ull) << L) >> (G + 1u));
     v.w = (int32_t)(uint32_t)val;
     store_rec(c, node, k.y, v, cell);
-    atomicOr(grid_words(c, m.grid) + (cell >> 5), 1u << (cell & 31u));
+    atomicOr(grid_words(c, gref) + (cell >> 5), 1u << (cell & 31u));
     s->key = HASH_EMPTY;
     s->val = HASH_EMPTY;
   }
+  if ((unsigned long long)pool_top + n_tasks > c.max_chunks) {
+    if (t0 == 0) set_error(c, E_POOL);
+    return;
+  }
+  for (uint64_t q = t0; q < n_tasks; q += nthreads) c.pool[pool_top + q] = c.pending[q];
 }
 
-// -------------------------------------------------------------- phase: spill
-
-// Per split leaf (one block each, blocks striding over the splits): zero the
-// node's new grid, copy its stored points and their gidx into its spill
-// range with the node as cursor, hand its chunks to the pending-free list.
-__device__ void phase_spill(const Ctx& c, uint32_t s_lo, uint32_t s_hi, uint32_t block0,
-                            uint32_t nblocks) {
-  constexpr uint32_t ROUND = 1024;
-  __shared__ uint32_t refs[ROUND];
-  __shared__ uint32_t s_nch, s_free0, s_n, s_bad;
-  for (uint32_t e = s_lo + block0; e < s_hi; e += nblocks) {
-    const SplitEntry se = c.splits[e];
-    const uint32_t id = se.node;
-    if (id >= c.max_nodes || !ref_ok(c, c.meta[id].grid, c.grid_bytes) ||
-        (unsigned long long)se.spill_off + c.num[id] > c.spill_cap) {
-      if (threadIdx.x == 0) set_error(c, E_INTERNAL);
-      continue;
-    }
-    NodeMeta& m = c.meta[id];
-    int4* g = reinterpret_cast<int4*>(grid_words(c, m.grid));
-    for (uint32_t q = threadIdx.x; q < c.grid_bytes / 16u; q += blockDim.x)
-      g[q] = make_int4(0, 0, 0, 0);
-    if (threadIdx.x == 0) {
-      s_bad = 0;
-      s_nch = m.n_chunks;
-      s_n = c.num[id];
-      s_free0 = atomicAdd(&c.ctl->pending_free, m.n_chunks);
-      if ((unsigned long long)s_free0 + m.n_chunks > c.max_chunks) set_error(c, E_POOL);
-    }
-    __syncthreads();
-    const uint32_t nch = s_nch, n = s_n, free0 = s_free0;
-    const bool ok = (unsigned long long)free0 + nch <= c.max_chunks;
-    uint32_t walk = m.head;  // used by thread 0 only
-    for (uint32_t r0 = 0; r0 < nch; r0 += ROUND) {
-      const uint32_t cnt = min(ROUND, nch - r0);
-      if (threadIdx.x == 0) {
-        for (uint32_t q = 0; q < cnt; ++q) {
-          if (!ref_ok(c, walk, c.chunk_bytes)) {  // list shorter than n_chunks
-            set_error(c, E_INTERNAL);
-            s_bad = 1;
-            break;
-          }
-          refs[q] = walk;
-          walk = *chunk_next(c, walk);
-        }
-      }
-      __syncthreads();
-      if (s_bad) break;
-      const uint64_t lo = (uint64_t)r0 * c.C;
-      const uint64_t hi = min((uint64_t)n, (uint64_t)(r0 + cnt) * c.C);
-      for (uint64_t idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
-        const uint32_t j = (uint32_t)(idx / c.C), q = (uint32_t)(idx - (uint64_t)j * c.C);
-        const uint32_t ref = refs[j - r0];
-        const uint64_t dst = se.spill_off + idx;
-        c.sp_pt[dst] = chunk_recs(c, ref)[q];
-        c.sp_gidx[dst] = chunk_aux(c, ref)[q];
-        c.sp_cur[dst] = id;
-      }
-      if (ok)
-        for (uint32_t q = threadIdx.x; q < cnt; q += blockDim.x) c.pending[free0 + r0 + q] = refs[q];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      m.n_chunks = 0;
-      m.head = m.tail = NONE;
-      c.num[id] = 0;
-    }
-    __syncthreads();
-  }
-}
-
-// One block: move the chunks freed by this round's splits into the pool.
-__device__ void phase_merge_pending(const Ctx& c) {
-  __shared__ int top;
-  __shared__ uint32_t np;
-  if (threadIdx.x == 0) {
-    top = c.ctl->pool_top;
-    np = c.ctl->pending_free;
-    if ((unsigned long long)top + np > c.max_chunks) {
-      set_error(c, E_POOL);
-      np = 0;
-    }
-  }
-  __syncthreads();
-  for (uint32_t q = threadIdx.x; q < np; q += blockDim.x) c.pool[top + q] = c.pending[q];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    c.ctl->pool_top = top + (int)np;
-    c.ctl->pending_free = 0;
-  }
-  __syncthreads();
-}
-
-// One thread: close an applied update (advance gidx, fold the update into
-// the stats, clear the per-update counters).
+// One thread: close an applied update (advance gidx, return the freed
+// chunks to the pool, fold the update into the stats, clear the per-update
+// counters).
 __device__ void phase_end(const Ctx& c, uint64_t n, uint32_t iters) {
   Ctl* t = c.ctl;
   const unsigned long long nk =
       min((unsigned long long)t->nkeys, (unsigned long long)c.backlog_cap);
   t->base += n;
+  if ((unsigned long long)t->pool_top + t->ntasks <= c.max_chunks) t->pool_top += (int)t->ntasks;
   t->st_batches += 1;
   t->st_points += n;
   t->st_spilled += t->spill_count;
@@ -727,9 +778,10 @@ __device__ void phase_end(const Ctx& c, uint64_t n, uint32_t iters) {
   t->nkeys = 0;
   t->alloc_seq = 0;
   t->split_count = 0;
+  t->ntasks = 0;
 }
 
-// One thread: close a rejected update (decide already undid its counters).
+// One thread: close a rejected update (the rollback undid its counters).
 __device__ void phase_end_rejected(const Ctx& c) {
   Ctl* t = c.ctl;
   t->reject = 0;

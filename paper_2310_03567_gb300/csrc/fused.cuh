@@ -16,7 +16,7 @@
 namespace sl {
 
 constexpr unsigned long long FUSED_BARRIER_NS = 2000000000ull;  // 2 s
-constexpr int FUSED_BLOCK = 512;
+constexpr int FUSED_BLOCK = 1024;
 constexpr unsigned long long NO_BUDGET = ~0ull;
 constexpr uint32_t MAX_FUSED_BATCHES = 16384;
 
@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(FUSED_BLOCK) k_fused(Ctx c, const BatchDesc* b
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t warp0 = tid / 32, nwarps = nthreads / 32;
   const unsigned long long t_begin = globaltimer_ns();
+  extern __shared__ uint32_t smem[];  // node-table cache (NODE_CACHE_BYTES)
   for (uint32_t b = 0; b < n_batches; ++b) {
     // every value read here was written before the last barrier and is not
     // written again before the next one, so all threads decide alike
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(FUSED_BLOCK) k_fused(Ctx c, const BatchDesc* b
     const uint32_t nodes0 = vload(&c.ctl->n_nodes);
     bool rejected = false;
     if (bd.n) {
-      phase_count1(c, bd.pts, bd.n, base, warp0, nwarps);
+      phase_count1(c, smem, nodes0, bd.pts, bd.n, base, warp0, nwarps);
       if (!grid_barrier(c, f)) return;
       rejected = vload(&c.ctl->reject) != 0u;  // set only by the count round
       if (rejected) {
@@ -121,11 +122,14 @@ __global__ void __launch_bounds__(FUSED_BLOCK) k_fused(Ctx c, const BatchDesc* b
           f->rejected += 1;
         }
       } else {
-        uint32_t s_lo = 0, s_hi = 0, n_lo = 0, n_hi = nodes0, iters = 1;
+        // s: split-list range of the previous round, n: nodes it created,
+        // t: its spill tasks (tasks below t_lo are older)
+        uint32_t s_lo = 0, s_hi = 0, n_lo = 0, n_hi = nodes0, t_lo = 0, t_hi = 0, iters = 1;
         for (;;) {
           phase_decide(c, s_lo, s_hi, n_lo, n_hi, tid, nthreads);
           if (!grid_barrier(c, f)) return;
           const uint32_t sc = vload(&c.ctl->split_count), nn = vload(&c.ctl->n_nodes);
+          const uint32_t nt = vload(&c.ctl->ntasks);
           if (sc == s_hi) break;
           if (iters >= max_iters) {
             if (tid == 0) set_error(c, E_ITER_CAP);
@@ -135,17 +139,16 @@ __global__ void __launch_bounds__(FUSED_BLOCK) k_fused(Ctx c, const BatchDesc* b
           s_hi = sc;
           n_lo = n_hi;
           n_hi = nn;
+          t_lo = t_hi;
+          t_hi = nt;
           ++iters;
-          phase_spill(c, s_lo, s_hi, blockIdx.x, gridDim.x);
-          if (!grid_barrier(c, f)) return;
-          const uint32_t n_spill = vload(&c.ctl->spill_count);
-          if (blockIdx.x == 0) phase_merge_pending(c);
-          phase_advance(c, bd.pts, bd.n, base, n_spill, warp0, nwarps);
+          phase_advance(c, smem, nn, bd.pts, bd.n, base, t_lo, t_hi, s_lo, s_hi, warp0, nwarps);
           if (!grid_barrier(c, f)) return;
         }
-        const uint32_t n_spill = vload(&c.ctl->spill_count);
+        const uint32_t n_tasks = vload(&c.ctl->ntasks);
         const uint32_t n_keys = min(vload(&c.ctl->nkeys), c.backlog_cap);
-        phase_store(c, bd.pts, bd.n, base, n_spill, n_keys, tid, nthreads);
+        const int pool_top = vload(&c.ctl->pool_top);
+        phase_store(c, bd.pts, bd.n, base, n_tasks, n_keys, pool_top, tid, nthreads);
         if (!grid_barrier(c, f)) return;
         if (tid == 0) phase_end(c, bd.n, iters);
       }

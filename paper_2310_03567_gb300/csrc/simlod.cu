@@ -19,12 +19,14 @@ using namespace sl;
 namespace {
 
 constexpr int BLOCK = 256;
+constexpr int PBLOCK = 1024;  // count / advance kernels (one node-table cache per block)
 
 __global__ void k_init(Ctx c) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Ctl* t = c.ctl;
     memset(t, 0, sizeof(Ctl));
     t->n_nodes = 1;
+    t->bump = c.dir_bytes;  // the root's chunk directory is the first data ref
     NodeMeta m;
     memset(&m, 0, sizeof(m));
     m.min[0] = c.rmin[0];
@@ -32,10 +34,11 @@ __global__ void k_init(Ctx c) {
     m.min[2] = c.rmin[2];
     m.level = 0;
     m.head = m.tail = NONE;
-    m.grid = NONE;
+    m.dir = 0;
     m.st_tail = NONE;
     c.meta[0] = m;
     c.child[0] = NONE;
+    c.gridref[0] = NONE;
     c.cnt[0] = 0;
     c.num[0] = 0;
   }
@@ -49,10 +52,11 @@ __global__ void k_fill_hash(HSlot* h, uint64_t n) {
   }
 }
 
-__global__ void __launch_bounds__(BLOCK) k_count1(Ctx c, const int4* pts, uint64_t n,
-                                                   unsigned long long base) {
+__global__ void __launch_bounds__(PBLOCK) k_count1(Ctx c, const int4* pts, uint64_t n,
+                                                    unsigned long long base, uint32_t n_nodes) {
+  extern __shared__ uint32_t smem[];
   const uint64_t warps_per_block = blockDim.x / 32;
-  phase_count1(c, pts, n, base, blockIdx.x * warps_per_block + threadIdx.x / 32,
+  phase_count1(c, smem, n_nodes, pts, n, base, blockIdx.x * warps_per_block + threadIdx.x / 32,
                (uint64_t)gridDim.x * warps_per_block);
 }
 
@@ -69,24 +73,22 @@ __global__ void __launch_bounds__(BLOCK) k_decide(Ctx c, uint32_t s_lo, uint32_t
   phase_decide(c, s_lo, s_hi, n_lo, n_hi, t0, nt);
 }
 
-__global__ void __launch_bounds__(BLOCK) k_spill(Ctx c, uint32_t s_lo, uint32_t s_hi) {
-  phase_spill(c, s_lo, s_hi, blockIdx.x, gridDim.x);
-}
-
-__global__ void k_merge_pending(Ctx c) { phase_merge_pending(c); }
-
-__global__ void __launch_bounds__(BLOCK) k_advance(Ctx c, const int4* pts, uint64_t n,
-                                                    unsigned long long base, uint32_t n_spill) {
+__global__ void __launch_bounds__(PBLOCK) k_advance(Ctx c, const int4* pts, uint64_t n,
+                                                     unsigned long long base, uint32_t n_nodes,
+                                                     uint32_t t_lo, uint32_t t_hi, uint32_t s_lo,
+                                                     uint32_t s_hi) {
+  extern __shared__ uint32_t smem[];
   const uint64_t warps_per_block = blockDim.x / 32;
-  phase_advance(c, pts, n, base, n_spill, blockIdx.x * warps_per_block + threadIdx.x / 32,
+  phase_advance(c, smem, n_nodes, pts, n, base, t_lo, t_hi, s_lo, s_hi,
+                blockIdx.x * warps_per_block + threadIdx.x / 32,
                 (uint64_t)gridDim.x * warps_per_block);
 }
 
 __global__ void __launch_bounds__(BLOCK) k_store(Ctx c, const int4* pts, uint64_t n,
-                                                  unsigned long long base, uint32_t n_spill,
-                                                  uint32_t n_keys) {
-  phase_store(c, pts, n, base, n_spill, n_keys, blockIdx.x * (uint64_t)blockDim.x + threadIdx.x,
-              (uint64_t)gridDim.x * blockDim.x);
+                                                  unsigned long long base, uint32_t n_tasks,
+                                                  uint32_t n_keys, int pool_top) {
+  phase_store(c, pts, n, base, n_tasks, n_keys, pool_top,
+              blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
 
 __global__ void k_end(Ctx c, uint64_t n, uint32_t iters) { phase_end(c, n, iters); }
@@ -97,13 +99,13 @@ __global__ void k_end_rejected(Ctx c) { phase_end_rejected(c); }
 
 // ================================================================ host side
 
-enum KernelId { K_COUNT = 0, K_DECIDE, K_SPILL, K_MERGE, K_ADVANCE, K_STORE, K_END, K_FUSED };
+enum KernelId { K_COUNT = 0, K_DECIDE, K_ADVANCE, K_STORE, K_END, K_FUSED, K_INIT, K_UNUSED };
 static const char* const kKernelNames[SIMLOD_N_KERNELS] = {
-    "count1", "decide", "spill", "merge_pending", "advance", "store", "end", "fused_update"};
+    "count1", "decide", "advance", "store", "end", "fused_update", "init", "unused"};
 
 struct Layout {
-  size_t ctl, fctl, batches, child, cnt, num, meta, pool, pending, alloc_refs, splits, sp_pt,
-      sp_gidx, sp_cur, sp_slot, b_cur, b_slot, hash, keys, staging, data, end;
+  size_t ctl, fctl, batches, child, gridref, cnt, num, meta, pool, pending, alloc_refs, splits,
+      tasks, sp_cur, sp_slot, b_cur, b_slot, hash, keys, staging, data, end;
   uint64_t hash_slots, max_chunks, max_splits, data_bytes;
 };
 
@@ -160,6 +162,8 @@ bool valid_config(const simlod_config* c) {
       c->backlog_capacity > (1ull << 31))
     return false;
   if (c->max_nodes < 9 || c->max_nodes > (1ull << 31)) return false;
+  if ((c->leaf_capacity + (uint64_t)c->chunk_points - 1) / c->chunk_points > (1u << 18))
+    return false;  // chunk directories of at most 1 MiB
   for (int a = 0; a < 3; ++a) {
     long long hi = (long long)c->root_min[a] + (1ll << c->root_log2) - 1;
     if (hi > 0x7FFFFFFFll) return false;
@@ -169,6 +173,16 @@ bool valid_config(const simlod_config* c) {
 
 uint32_t chunk_bytes_of(const simlod_config* c) {
   return (uint32_t)align_up(CHUNK_HEADER + 20ull * c->chunk_points, REF_BYTES);
+}
+
+// A leaf's chunk directory holds one ref per chunk; a leaf that can still
+// split holds at most T points, so ceil(T / C) + 1 entries suffice.
+uint32_t dir_cap_of(const simlod_config* c) {
+  return (uint32_t)((c->leaf_capacity + (uint64_t)c->chunk_points - 1) / c->chunk_points + 1);
+}
+
+uint32_t dir_bytes_of(const simlod_config* c) {
+  return (uint32_t)align_up(4ull * dir_cap_of(c), REF_BYTES);
 }
 
 uint32_t grid_bytes_of(const simlod_config* c) {
@@ -192,12 +206,11 @@ bool plan_layout(const simlod_config* c, size_t arena_bytes, Layout* L) {
   L->fctl = take(sizeof(FusedCtl));
   L->batches = take(sizeof(BatchDesc) * MAX_FUSED_BATCHES);
   L->child = take(4 * N);
+  L->gridref = take(4 * N);
   L->cnt = take(4 * N);
   L->num = take(4 * N);
   L->meta = take(sizeof(NodeMeta) * N);
   L->splits = take(sizeof(SplitEntry) * L->max_splits);
-  L->sp_pt = take(16 * S);
-  L->sp_gidx = take(4 * S);
   L->sp_cur = take(4 * S);
   L->sp_slot = take(4 * S);
   L->b_cur = take(4 * B);
@@ -208,12 +221,14 @@ bool plan_layout(const simlod_config* c, size_t arena_bytes, Layout* L) {
   const size_t fixed = align_up(o, 256);
   if (arena_bytes < fixed) return false;
   const uint64_t cb = chunk_bytes_of(c);
-  uint64_t max_chunks = (arena_bytes - fixed) / (cb + 12);
+  // per chunk of the data region: pool, pending, alloc_refs (4 B each) and a task (16 B)
+  uint64_t max_chunks = (arena_bytes - fixed) / (cb + 28);
   if (max_chunks > 0xFFFFFFF0ull) max_chunks = 0xFFFFFFF0ull;
   L->max_chunks = max_chunks;
   L->pool = take(4 * max_chunks);
   L->pending = take(4 * max_chunks);
   L->alloc_refs = take(4 * max_chunks);
+  L->tasks = take(sizeof(SpillTask) * max_chunks);
   L->data = align_up(o, 256);
   if (arena_bytes < L->data) return false;
   L->data_bytes = (arena_bytes - L->data) / REF_BYTES * REF_BYTES;
@@ -230,6 +245,7 @@ void make_ctx(simlod_t* h) {
   h->fctl_dev = reinterpret_cast<FusedCtl*>(a + L.fctl);
   h->batches_dev = reinterpret_cast<BatchDesc*>(a + L.batches);
   c.child = reinterpret_cast<uint32_t*>(a + L.child);
+  c.gridref = reinterpret_cast<uint32_t*>(a + L.gridref);
   c.cnt = reinterpret_cast<uint32_t*>(a + L.cnt);
   c.num = reinterpret_cast<uint32_t*>(a + L.num);
   c.meta = reinterpret_cast<NodeMeta*>(a + L.meta);
@@ -237,8 +253,7 @@ void make_ctx(simlod_t* h) {
   c.pending = reinterpret_cast<uint32_t*>(a + L.pending);
   c.alloc_refs = reinterpret_cast<uint32_t*>(a + L.alloc_refs);
   c.splits = reinterpret_cast<SplitEntry*>(a + L.splits);
-  c.sp_pt = reinterpret_cast<int4*>(a + L.sp_pt);
-  c.sp_gidx = reinterpret_cast<uint32_t*>(a + L.sp_gidx);
+  c.tasks = reinterpret_cast<SpillTask*>(a + L.tasks);
   c.sp_cur = reinterpret_cast<uint32_t*>(a + L.sp_cur);
   c.sp_slot = reinterpret_cast<uint32_t*>(a + L.sp_slot);
   c.b_cur = reinterpret_cast<uint32_t*>(a + L.b_cur);
@@ -257,6 +272,8 @@ void make_ctx(simlod_t* h) {
   c.chunk_bytes = chunk_bytes_of(&g);
   c.chunk_units = c.chunk_bytes / REF_BYTES;
   c.grid_bytes = grid_bytes_of(&g);
+  c.dir_bytes = dir_bytes_of(&g);
+  c.dir_cap = dir_cap_of(&g);
   c.hash_mask = (uint32_t)(L.hash_slots - 1);
   c.max_nodes = (uint32_t)g.max_nodes;
   c.max_chunks = (uint32_t)L.max_chunks;
@@ -357,9 +374,11 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
   const Ctx& c = h->ctx;
   const unsigned long long base = h->base;
   const uint32_t nodes0 = h->n_nodes;
-  const unsigned gp = grid_for(h, n, BLOCK);
+  const unsigned gp = std::max(1u, std::min<unsigned>(grid_for(h, n, PBLOCK), 2u * h->sm_count));
   int rc;
-  rc = launch(h, K_COUNT, s, [&] { k_count1<<<gp, BLOCK, 0, s>>>(c, pts, n, base); });
+  rc = launch(h, K_COUNT, s, [&] {
+    k_count1<<<gp, PBLOCK, NODE_CACHE_BYTES, s>>>(c, pts, n, base, nodes0);
+  });
   if (rc) return poison(h, rc);
   rc = launch(h, K_DECIDE, s, [&] {
     k_decide<<<grid_for(h, nodes0, BLOCK), BLOCK, 0, s>>>(c, 0, 0, 0, nodes0);
@@ -375,18 +394,18 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
   }
   const uint32_t max_iters = h->cfg.max_expand_iters ? h->cfg.max_expand_iters
                                                       : h->cfg.root_log2 + 1;
-  uint32_t s_lo = 0, s_hi = t.split_count, n_lo = nodes0, n_hi = t.n_nodes, iters = 1;
+  // s: split-list range of the previous round, n: nodes it created,
+  // t: its spill tasks (tasks below t_lo are older)
+  uint32_t s_lo = 0, s_hi = t.split_count, n_lo = nodes0, n_hi = t.n_nodes, t_lo = 0,
+           t_hi = t.ntasks, iters = 1;
   while (s_hi > s_lo) {
     if (iters >= max_iters) return poison(h, SIMLOD_ERR_ITER_CAP);
-    const uint32_t n_spill = h->ctl_host->spill_count;
-    rc = launch(h, K_SPILL, s, [&] {
-      k_spill<<<std::min<uint32_t>(s_hi - s_lo, 65535u), BLOCK, 0, s>>>(c, s_lo, s_hi);
-    });
-    if (rc) return poison(h, rc);
-    rc = launch(h, K_MERGE, s, [&] { k_merge_pending<<<1, 1024, 0, s>>>(c); });
-    if (rc) return poison(h, rc);
+    const uint64_t units = (n + 31) / 32 + (uint64_t)t_hi * 8 + (uint64_t)(s_hi - s_lo) * 64;
+    const unsigned ga =
+        std::max(1u, std::min<unsigned>(grid_for(h, units * 32, PBLOCK), 2u * h->sm_count));
+    const uint32_t nn = n_hi;
     rc = launch(h, K_ADVANCE, s, [&] {
-      k_advance<<<grid_for(h, n + n_spill, BLOCK), BLOCK, 0, s>>>(c, pts, n, base, n_spill);
+      k_advance<<<ga, PBLOCK, NODE_CACHE_BYTES, s>>>(c, pts, n, base, nn, t_lo, t_hi, s_lo, s_hi);
     });
     if (rc) return poison(h, rc);
     const uint64_t cand = (uint64_t)(s_hi - s_lo) + (n_hi - n_lo);
@@ -400,13 +419,17 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
     s_hi = h->ctl_host->split_count;
     n_lo = n_hi;
     n_hi = h->ctl_host->n_nodes;
+    t_lo = t_hi;
+    t_hi = h->ctl_host->ntasks;
     ++iters;
   }
-  const uint32_t n_spill = h->ctl_host->spill_count;
+  const uint32_t n_tasks = h->ctl_host->ntasks;
   const uint32_t n_keys = std::min<uint32_t>(h->ctl_host->nkeys, c.backlog_cap);
+  const int pool_top = h->ctl_host->pool_top;
+  const uint64_t work = std::max<uint64_t>(std::max<uint64_t>(n, (uint64_t)n_tasks * c.C), n_keys);
   rc = launch(h, K_STORE, s, [&] {
-    k_store<<<grid_for(h, std::max<uint64_t>(n + n_spill, n_keys), BLOCK), BLOCK, 0, s>>>(
-        c, pts, n, base, n_spill, n_keys);
+    k_store<<<grid_for(h, work, BLOCK), BLOCK, 0, s>>>(c, pts, n, base, n_tasks, n_keys,
+                                                      pool_top);
   });
   if (rc) return poison(h, rc);
   rc = launch(h, K_END, s, [&] { k_end<<<1, 1, 0, s>>>(c, n, iters); });
@@ -446,7 +469,7 @@ int launch_fused(simlod_t* h, const simlod_point* const* d_batches, const uint64
   cudaError_t le = cudaSuccess;
   int rc = launch(h, K_FUSED, s, [&] {
     le = cudaLaunchCooperativeKernel((const void*)k_fused, dim3(h->fused_grid),
-                                     dim3(FUSED_BLOCK), args, 0, s);
+                                     dim3(FUSED_BLOCK), args, NODE_CACHE_BYTES, s);
   });
   if (rc || le != cudaSuccess) return poison(h, SIMLOD_ERR_CUDA);
   h->base += total;  // upper bound until the next control-block read
@@ -515,7 +538,7 @@ SIMLOD_API int simlod_arena_bytes(const simlod_config* cfg, uint64_t data_bytes,
   plan_layout(cfg, 0, &L);  // fixed part only
   size_t o = L.staging + 16 * cfg->max_batch_points;
   uint64_t chunks = data_bytes / chunk_bytes_of(cfg) + 1;
-  o = align_up(o, 256) + align_up(4 * chunks, 256) * 3 + 256;
+  o = align_up(o, 256) + align_up(4 * chunks, 256) * 3 + align_up(16 * chunks, 256) + 256;
   *arena_bytes = align_up(o + data_bytes, 256) + 256;
   return SIMLOD_OK;
 }
@@ -544,10 +567,20 @@ SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t are
     return SIMLOD_ERR_CUDA;
   }
   memset(h->ctl_host, 0, sizeof(Ctl));
+  if (cudaFuncSetAttribute(k_count1, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           NODE_CACHE_BYTES) != cudaSuccess ||
+      cudaFuncSetAttribute(k_advance, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           NODE_CACHE_BYTES) != cudaSuccess ||
+      cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           NODE_CACHE_BYTES) != cudaSuccess) {
+    cudaFreeHost(h->ctl_host);
+    delete h;
+    return SIMLOD_ERR_CUDA;
+  }
   int coop = 0, bpsm = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_fused, FUSED_BLOCK, 0) ==
-                  cudaSuccess)
+  if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_fused, FUSED_BLOCK,
+                                                             NODE_CACHE_BYTES) == cudaSuccess)
     h->fused_grid = std::min(bpsm, 4) * h->sm_count;
   if (cudaMallocHost(reinterpret_cast<void**>(&h->desc_host),
                      sizeof(BatchDesc) * MAX_FUSED_BATCHES) != cudaSuccess ||
