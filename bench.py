@@ -179,6 +179,33 @@ def run_reference(args):
     return 0
 
 
+def rank_workload(name: str, points, rank: int):
+    """The workload a rank builds: every rank has its own octree and stream
+    (independent units, no data-path collective); rank r > 0 gets its own
+    seed so that the replicas are not copies."""
+    w, root_log2 = make_workload(name, points)
+    if rank:
+        from paper_2310_03567_gb300 import synth
+        if name == "aerial":
+            w.points = synth.terrain(1 + 1000 * rank, w.n_points)
+        elif name == "uniform":
+            w.points = synth.uniform(1000 * rank, 1_000_000, w.n_points)
+    return w, root_log2
+
+
+def aggregate(ms_local: float, points_local: int, dist=None, device="cpu"):
+    """Whole-job timing across ranks: the slowest rank's time and the total
+    points of all ranks (value = total / max time)."""
+    if dist is None:
+        return ms_local, points_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    p = torch.tensor([points_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(p.item())
+
+
 def percentile(v, q):
     if not v:
         return None
@@ -205,19 +232,18 @@ def run_ours(args):
     simlod.load()
 
     # each rank builds its own octree from its own stream (independent units)
-    w, root_log2 = make_workload(args.workload, args.points)
-    if rank:
-        from paper_2310_03567_gb300 import synth
-        if args.workload == "aerial":
-            w.points = synth.terrain(1 + 1000 * rank, w.n_points)
+    w, root_log2 = rank_workload(args.workload, args.points, rank)
     n_points = w.n_points
     dev_pts = simlod.points_tensor(w.points)
     ptrs = [dev_pts.data_ptr() + int(o) * 16 for o in w.offsets]
     counts = [int(c) for c in w.counts]
     max_batch = max(counts)
+    # claim table: 2 slots per backlog entry; up to 2 new voxels per batch
+    # point keeps the table (64 MB for 1M-point batches) mostly L2-resident
     cfg = simlod.default_config(root_min=w.root_min, root_log2=root_log2,
                                 max_batch_points=max_batch,
                                 spill_capacity=max(8 << 20, 2 * max_batch),
+                                backlog_capacity=max(2 << 20, 2 * max_batch),
                                 max_nodes=1 << 21)
     data_bytes = max(256 << 20, n_points * 80)
     arena = simlod.make_arena(cfg, data_bytes)
@@ -267,11 +293,8 @@ def run_ours(args):
     tree.set_timing(False)
     clk = clocks.stop()
     check(tree.sync(), "timed steps")
-    ms_total = ev0.elapsed_time(ev1)
+    ms_total, job_points = aggregate(ev0.elapsed_time(ev1), n_points, dist, "cuda")
     if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
         dist.barrier()
     ktime = tree.timing()
 
@@ -335,7 +358,7 @@ def run_ours(args):
     avg_ms = f_ms / max(f_launches, 1)
     achieved = upd_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms else 0.0
     ms_per_step = ms_total / args.steps
-    value = n_points * world * args.steps / (ms_total * 1e-3) / 1e6
+    value = job_points * args.steps / (ms_total * 1e-3) / 1e6
     roofline_mpts = B / (upd_bytes / (peak * 1e9)) / 1e6
 
     line = {
@@ -360,7 +383,7 @@ def run_ours(args):
                             "frac": value / world / roofline_mpts},
         "update_counts": {"B": B, "S": S, "V": V, "K": K},
         "gpu_launches": 2 * args.steps,
-        "e2e": {"value": n_points * world / e2e_s / 1e6, "unit": UNIT,
+        "e2e": {"value": job_points / e2e_s / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": n_points * 16 + 16 * len(ptrs),
                 "d2h_bytes_per_step": CTL_BYTES},
         "clocks": clk,

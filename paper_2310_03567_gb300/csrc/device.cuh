@@ -48,10 +48,29 @@ constexpr uint32_t FULL_MASK = 0xFFFFFFFFu;
 constexpr int MAX_PROBES = 1 << 14;
 constexpr uint32_t REF_BYTES = 256;  // chunk, grid and directory references count 256-byte units
 constexpr uint32_t CHUNK_HEADER = 16;
-constexpr uint32_t NODE_CACHE = 12288;                 // nodes mirrored in shared memory
+// Launch-shape and algorithm knobs (compile-time; -D overrides them).
+#ifndef SL_NODE_CACHE
+#define SL_NODE_CACHE 8192
+#endif
+#ifndef SL_DESCENT_GROUP
+#define SL_DESCENT_GROUP 4
+#endif
+#ifndef SL_PHASE_BLOCK
+#define SL_PHASE_BLOCK 512
+#endif
+#ifndef SL_PHASE_MIN_BLOCKS
+#define SL_PHASE_MIN_BLOCKS 3
+#endif
+#ifndef SL_CAS128
+#define SL_CAS128 0
+#endif
+constexpr uint32_t NODE_CACHE = SL_NODE_CACHE;         // nodes mirrored in shared memory
 constexpr uint32_t NODE_CACHE_BYTES = NODE_CACHE * 8;  // child + grid reference
 constexpr uint32_t TASK_PART = 128;                    // points of a spill task per warp unit
 constexpr uint32_t ZERO_UNIT = 4096;                   // bytes of grid zeroed per warp unit
+constexpr int DESCENT_GROUP = SL_DESCENT_GROUP;        // levels whose grid words load together
+constexpr int PHASE_BLOCK = SL_PHASE_BLOCK;            // threads of count / advance / fused blocks
+constexpr int PHASE_MIN_BLOCKS = SL_PHASE_MIN_BLOCKS;  // resident blocks per SM they aim for
 
 // Sticky device error bits.
 enum : uint32_t {
@@ -103,7 +122,7 @@ struct NodeMeta {
 };
 static_assert(sizeof(NodeMeta) == 64, "NodeMeta size");
 
-struct HSlot {
+struct __align__(16) HSlot {
   unsigned long long key;  // (node << 3G) | cell, HASH_EMPTY when free
   unsigned long long val;  // (gidx << 32) | rgba of the best contender so far
 };
@@ -266,15 +285,34 @@ __device__ __forceinline__ uint32_t node_grid(const Ctx& c, NodeCache nc, uint32
 
 // Offer val = (gidx << 32 | rgba) as the colour of cell `key`; the lowest
 // gidx wins. Returns true, with the table slot in h, when this call put the
-// key into the table (the cell is new in this update).
+// key into the table (the cell is new in this update). A free slot takes key
+// and value in one 16-byte compare-and-swap; a slot holding the key is
+// lowered with atomicMin only when this value is smaller.
 __device__ __forceinline__ bool hash_claim(const Ctx& c, unsigned long long key,
                                            unsigned long long val, uint32_t& h) {
   h = (uint32_t)fmix64(key) & c.hash_mask;
+#if SL_CAS128
+  HSlot empty, mine;
+  empty.key = HASH_EMPTY;
+  empty.val = HASH_EMPTY;
+  mine.key = key;
+  mine.val = val;
+  for (int probe = 0; probe < MAX_PROBES; ++probe) {
+    HSlot* s = c.hash + h;
+    const HSlot old = atomicCAS(s, empty, mine);
+    if (old.key == HASH_EMPTY) return true;
+    if (old.key == key) {
+      if (old.val > val) atomicMin(&s->val, val);
+      return false;
+    }
+    h = (h + 1u) & c.hash_mask;
+  }
+#else
   for (int probe = 0; probe < MAX_PROBES; ++probe) {
     HSlot* s = c.hash + h;
     unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&s->key);
     if (k == HASH_EMPTY) {
-      unsigned long long old = atomicCAS(&s->key, HASH_EMPTY, key);
+      const unsigned long long old = atomicCAS(&s->key, HASH_EMPTY, key);
       if (old == HASH_EMPTY) {
         atomicMin(&s->val, val);
         return true;
@@ -287,6 +325,7 @@ __device__ __forceinline__ bool hash_claim(const Ctx& c, unsigned long long key,
     }
     h = (h + 1u) & c.hash_mask;
   }
+#endif
   set_error(c, E_BACKLOG);
   return false;
 }
@@ -366,31 +405,43 @@ __device__ void phase_count1(const Ctx& c, uint32_t* smem, uint32_t n_nodes, con
     uint32_t node = 0, L = c.rlog2;
     bool walking = valid;
     while (__any_sync(FULL_MASK, walking)) {
-      bool inner = false, want = false;
-      uint32_t cell = 0, nxt = 0;
-      if (walking) {
-        const uint32_t ch = node_child(c, nc, node);
-        if (ch == NONE) {
-          walking = false;
-        } else {
-          cell = cell_index(rx, ry, rz, L, c.G);
-          const uint32_t gref = node_grid(c, nc, node);
-          nxt = ch + octant(rx, ry, rz, L);
-          if (!ref_ok(c, gref, c.grid_bytes) || nxt >= c.max_nodes) {
-            set_error(c, E_INTERNAL);
+      // Walk up to DESCENT_GROUP levels through the node table first and
+      // issue their grid-word loads together (their addresses do not depend
+      // on each other), then test the bits and claim level by level.
+      uint32_t gnode[DESCENT_GROUP], gcell[DESCENT_GROUP], gword[DESCENT_GROUP];
+      bool ginner[DESCENT_GROUP];
+#pragma unroll
+      for (int k = 0; k < DESCENT_GROUP; ++k) {
+        ginner[k] = false;
+        gnode[k] = node;
+        gcell[k] = 0;
+        gword[k] = 0;
+        if (walking) {
+          const uint32_t ch = node_child(c, nc, node);
+          if (ch == NONE) {
             walking = false;
           } else {
-            inner = true;
-            const uint32_t word = grid_words(c, gref)[cell >> 5];
-            want = ((word >> (cell & 31u)) & 1u) == 0u;
+            const uint32_t gref = node_grid(c, nc, node);
+            const uint32_t cell = cell_index(rx, ry, rz, L, c.G);
+            const uint32_t nxt = ch + octant(rx, ry, rz, L);
+            if (!ref_ok(c, gref, c.grid_bytes) || nxt >= c.max_nodes) {
+              set_error(c, E_INTERNAL);
+              walking = false;
+            } else {
+              ginner[k] = true;
+              gcell[k] = cell;
+              gword[k] = grid_words(c, gref)[cell >> 5];
+              node = nxt;
+              --L;
+            }
           }
         }
       }
-      warp_claim(c, want, ((unsigned long long)node << (3u * c.G)) | cell, gidx, (uint32_t)p.w,
-                 node);
-      if (inner) {
-        node = nxt;
-        --L;
+#pragma unroll
+      for (int k = 0; k < DESCENT_GROUP; ++k) {
+        const bool want = ginner[k] && ((gword[k] >> (gcell[k] & 31u)) & 1u) == 0u;
+        warp_claim(c, want, ((unsigned long long)gnode[k] << (3u * c.G)) | gcell[k], gidx,
+                   (uint32_t)p.w, gnode[k]);
       }
     }
     uint32_t slot = warp_count(c, valid, node);
@@ -501,19 +552,14 @@ __device__ void phase_advance(const Ctx& c, uint32_t* smem, uint32_t n_nodes, co
 // ------------------------------------------------------------ phase: decide
 
 // Take up to k refs from the pool; returns how many and the first index.
+// One atomicSub per allocation: the top may go below zero while the pool is
+// empty; store and end clamp it at zero.
 __device__ __forceinline__ uint32_t pool_take(const Ctx& c, uint32_t k, int* first) {
-  int t = *reinterpret_cast<volatile int*>(&c.ctl->pool_top);
-  for (int it = 0; it < (1 << 20) && t > 0; ++it) {
-    int take = t < (int)k ? t : (int)k;
-    int old = atomicCAS(&c.ctl->pool_top, t, t - take);
-    if (old == t) {
-      *first = t - take;
-      return (uint32_t)take;
-    }
-    t = old;
-  }
-  if (t > 0) set_error(c, E_POOL);
-  return 0;
+  const int t = atomicSub(&c.ctl->pool_top, (int)k);
+  if (t <= 0) return 0;
+  const int take = t < (int)k ? t : (int)k;
+  *first = t - take;
+  return (uint32_t)take;
 }
 
 // Section 5.3: give node `id` ceil(total / C) chunks, pool first, then the
@@ -746,11 +792,12 @@ __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned 
     s->key = HASH_EMPTY;
     s->val = HASH_EMPTY;
   }
-  if ((unsigned long long)pool_top + n_tasks > c.max_chunks) {
+  const int top = pool_top > 0 ? pool_top : 0;
+  if ((unsigned long long)top + n_tasks > c.max_chunks) {
     if (t0 == 0) set_error(c, E_POOL);
     return;
   }
-  for (uint64_t q = t0; q < n_tasks; q += nthreads) c.pool[pool_top + q] = c.pending[q];
+  for (uint64_t q = t0; q < n_tasks; q += nthreads) c.pool[top + q] = c.pending[q];
 }
 
 // One thread: close an applied update (advance gidx, return the freed
@@ -761,7 +808,8 @@ __device__ void phase_end(const Ctx& c, uint64_t n, uint32_t iters) {
   const unsigned long long nk =
       min((unsigned long long)t->nkeys, (unsigned long long)c.backlog_cap);
   t->base += n;
-  if ((unsigned long long)t->pool_top + t->ntasks <= c.max_chunks) t->pool_top += (int)t->ntasks;
+  const int top = t->pool_top > 0 ? t->pool_top : 0;
+  t->pool_top = ((unsigned long long)top + t->ntasks <= c.max_chunks) ? top + (int)t->ntasks : top;
   t->st_batches += 1;
   t->st_points += n;
   t->st_spilled += t->spill_count;

@@ -16,7 +16,7 @@
 namespace sl {
 
 constexpr unsigned long long FUSED_BARRIER_NS = 2000000000ull;  // 2 s
-constexpr int FUSED_BLOCK = 1024;
+constexpr int FUSED_BLOCK = PHASE_BLOCK;
 constexpr unsigned long long NO_BUDGET = ~0ull;
 constexpr uint32_t MAX_FUSED_BATCHES = 16384;
 
@@ -92,7 +92,7 @@ __device__ __forceinline__ bool grid_barrier(const Ctx& c, FusedCtl* f) {
 // batch other than the first, stop once more than budget_ns has passed since
 // the launch began (Section 7.2's frame budget; batches are never cut);
 // NO_BUDGET disables the check.
-__global__ void __launch_bounds__(FUSED_BLOCK) k_fused(Ctx c, const BatchDesc* batches,
+__global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, const BatchDesc* batches,
                                                         uint32_t n_batches, FusedCtl* f,
                                                         unsigned long long budget_ns,
                                                         uint32_t max_iters) {

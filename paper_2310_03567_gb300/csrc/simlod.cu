@@ -19,7 +19,7 @@ using namespace sl;
 namespace {
 
 constexpr int BLOCK = 256;
-constexpr int PBLOCK = 1024;  // count / advance kernels (one node-table cache per block)
+constexpr int PBLOCK = PHASE_BLOCK;  // count / advance kernels (one node-table cache per block)
 
 __global__ void k_init(Ctx c) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -52,7 +52,7 @@ __global__ void k_fill_hash(HSlot* h, uint64_t n) {
   }
 }
 
-__global__ void __launch_bounds__(PBLOCK) k_count1(Ctx c, const int4* pts, uint64_t n,
+__global__ void __launch_bounds__(PBLOCK, PHASE_MIN_BLOCKS) k_count1(Ctx c, const int4* pts, uint64_t n,
                                                     unsigned long long base, uint32_t n_nodes) {
   extern __shared__ uint32_t smem[];
   const uint64_t warps_per_block = blockDim.x / 32;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(BLOCK) k_decide(Ctx c, uint32_t s_lo, uint32_t
   phase_decide(c, s_lo, s_hi, n_lo, n_hi, t0, nt);
 }
 
-__global__ void __launch_bounds__(PBLOCK) k_advance(Ctx c, const int4* pts, uint64_t n,
+__global__ void __launch_bounds__(PBLOCK, PHASE_MIN_BLOCKS) k_advance(Ctx c, const int4* pts, uint64_t n,
                                                      unsigned long long base, uint32_t n_nodes,
                                                      uint32_t t_lo, uint32_t t_hi, uint32_t s_lo,
                                                      uint32_t s_hi) {
@@ -374,7 +374,7 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
   const Ctx& c = h->ctx;
   const unsigned long long base = h->base;
   const uint32_t nodes0 = h->n_nodes;
-  const unsigned gp = std::max(1u, std::min<unsigned>(grid_for(h, n, PBLOCK), 2u * h->sm_count));
+  const unsigned gp = std::max(1u, std::min<unsigned>(grid_for(h, n, PBLOCK), (unsigned)PHASE_MIN_BLOCKS * h->sm_count));
   int rc;
   rc = launch(h, K_COUNT, s, [&] {
     k_count1<<<gp, PBLOCK, NODE_CACHE_BYTES, s>>>(c, pts, n, base, nodes0);
@@ -402,7 +402,7 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
     if (iters >= max_iters) return poison(h, SIMLOD_ERR_ITER_CAP);
     const uint64_t units = (n + 31) / 32 + (uint64_t)t_hi * 8 + (uint64_t)(s_hi - s_lo) * 64;
     const unsigned ga =
-        std::max(1u, std::min<unsigned>(grid_for(h, units * 32, PBLOCK), 2u * h->sm_count));
+        std::max(1u, std::min<unsigned>(grid_for(h, units * 32, PBLOCK), (unsigned)PHASE_MIN_BLOCKS * h->sm_count));
     const uint32_t nn = n_hi;
     rc = launch(h, K_ADVANCE, s, [&] {
       k_advance<<<ga, PBLOCK, NODE_CACHE_BYTES, s>>>(c, pts, n, base, nn, t_lo, t_hi, s_lo, s_hi);
