@@ -29,7 +29,7 @@ if REPO not in sys.path:
 METRIC = "Mpts/s inserted into octree (frac. of HBM roofline); p50/p99 batch latency vs plain"
 UNIT = "Mpts/s"
 L2_BYTES = 129 << 20
-CTL_BYTES = 192  # the library's control block, read once per expansion round
+CTL_BYTES = 256  # the library's control block, read once per expansion round
 
 # Algorithmic bytes of one update: read every batch point (16 B), write
 # every point with its gidx (20 B), read and rewrite every re-inserted point
@@ -297,6 +297,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     ktime = tree.timing()
+    phases = {k: v / args.steps for k, v in tree.phase_times().items() if v > 0}
 
     # ---- per-batch latency: fused form one launch per batch, and plain form
     lat_fused = []
@@ -382,6 +383,7 @@ def run_ours(args):
         "update_roofline": {"alg_bytes_per_point": upd_bytes / B, "roofline_mpts": roofline_mpts,
                             "frac": value / world / roofline_mpts},
         "update_counts": {"B": B, "S": S, "V": V, "K": K},
+        "fused_phase_ms_per_step": phases,
         "gpu_launches": 2 * args.steps,
         "e2e": {"value": job_points / e2e_s / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": n_points * 16 + 16 * len(ptrs),

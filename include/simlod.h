@@ -118,12 +118,17 @@ typedef struct {
   uint32_t device_error_bits;
 } simlod_stats;
 
-/* Per-kernel device time, accumulated while timing is enabled. */
+/* Per-kernel device time, accumulated while timing is enabled, and the
+ * time the fused form spent per phase (measured on the GPU timer between
+ * its grid barriers, accumulated since create/reset or the last clear). */
 #define SIMLOD_N_KERNELS 8
+#define SIMLOD_N_PHASES 8
 typedef struct {
   const char* name[SIMLOD_N_KERNELS];
   uint64_t launches[SIMLOD_N_KERNELS];
   double ms[SIMLOD_N_KERNELS];
+  const char* phase_name[SIMLOD_N_PHASES];
+  double phase_ms[SIMLOD_N_PHASES];
 } simlod_timing;
 
 enum {

@@ -69,8 +69,11 @@ constexpr uint32_t NODE_CACHE_BYTES = NODE_CACHE * 8;  // child + grid reference
 constexpr uint32_t TASK_PART = 128;                    // points of a spill task per warp unit
 constexpr uint32_t ZERO_UNIT = 4096;                   // bytes of grid zeroed per warp unit
 constexpr int DESCENT_GROUP = SL_DESCENT_GROUP;        // levels whose grid words load together
+constexpr uint32_t WBUF = 64;                          // new-cell slots staged per warp
 constexpr int PHASE_BLOCK = SL_PHASE_BLOCK;            // threads of count / advance / fused blocks
 constexpr int PHASE_MIN_BLOCKS = SL_PHASE_MIN_BLOCKS;  // resident blocks per SM they aim for
+// dynamic shared memory of the count / advance / fused blocks
+constexpr uint32_t PHASE_SMEM_BYTES = NODE_CACHE_BYTES + (PHASE_BLOCK / 32) * WBUF * 4;
 
 // Sticky device error bits.
 enum : uint32_t {
@@ -105,8 +108,12 @@ struct Ctl {
   unsigned long long last_points, last_spilled, last_splits, last_voxels, last_iters;
   unsigned long long st_rejected_async;  // rejections inside fused launches
   unsigned long long pad1[2];
+  unsigned long long phase_ns[8];        // fused form: time per phase (see PH_*)
 };
 static_assert(sizeof(Ctl) % 16 == 0, "Ctl size");
+
+// Phases of the fused form, for its phase clock.
+enum : int { PH_COUNT = 0, PH_DECIDE, PH_ADVANCE, PH_STORE, PH_END, PH_ROLLBACK, PH_LAUNCH, PH_OTHER };
 
 // Per-node metadata that the count/advance hot loops do not touch.
 struct NodeMeta {
@@ -117,8 +124,9 @@ struct NodeMeta {
   uint32_t dir;         // chunk directory of a leaf (ref), NONE if none
   uint32_t st_nch;      // store map of the current update: chunks before allocation,
   uint32_t st_tail;     //   the tail before allocation,
-  uint32_t st_seq;      //   first alloc_refs entry of the newly allocated chunks
-  uint32_t pad[5];
+  uint32_t st_seq;      //   first alloc_refs entry of the newly allocated chunks,
+  uint32_t st_base;     //   and the records stored before this update
+  uint32_t pad[4];
 };
 static_assert(sizeof(NodeMeta) == 64, "NodeMeta size");
 
@@ -154,12 +162,11 @@ struct Ctx {
   uint32_t* alloc_refs;
   SplitEntry* splits;
   SpillTask* tasks;
-  uint32_t* sp_cur;   // per spill entry: cursor node and slot (after its first move)
-  uint32_t* sp_slot;
-  uint32_t* b_cur;
-  uint32_t* b_slot;
+  uint32_t* sp_cur;   // per spill entry: cursor node (after its first move)
+  uint32_t* b_cur;    // per batch point: cursor node
+  uint32_t* scur;     // per node: store cursor of the current update
   HSlot* hash;
-  uint2* keys;  // backlog: (hash slot, voxel slot)
+  uint32_t* keys;     // backlog: table slots of this update's new cells
   uint8_t* data;
   unsigned long long data_bytes;
   int4* staging;
@@ -330,13 +337,43 @@ __device__ __forceinline__ bool hash_claim(const Ctx& c, unsigned long long key,
   return false;
 }
 
+// Per-warp staging of the table slots of new cells (shared memory), flushed
+// to the backlog with one atomic per flush.
+struct WarpBuf {
+  uint32_t* buf;  // WBUF entries of this warp
+  uint32_t n;     // staged entries (the same value in every lane)
+};
+
+__device__ __forceinline__ WarpBuf warp_buf(uint32_t* smem) {
+  WarpBuf wb;
+  wb.buf = smem + 2 * NODE_CACHE + (threadIdx.x / 32) * WBUF;
+  wb.n = 0;
+  return wb;
+}
+
+// All 32 lanes call: append the staged slots to the backlog.
+__device__ __forceinline__ void warp_flush(const Ctx& c, WarpBuf& wb) {
+  if (wb.n == 0u) return;
+  __syncwarp();
+  uint32_t e0 = 0;
+  if (lane_id() == 0) e0 = atomicAdd(&c.ctl->nkeys, wb.n);
+  e0 = __shfl_sync(FULL_MASK, e0, 0);
+  for (uint32_t k = lane_id(); k < wb.n; k += 32) {
+    const uint32_t e = e0 + k;
+    if (e < c.backlog_cap) c.keys[e] = wb.buf[k];
+    else set_error(c, E_BACKLOG);
+  }
+  wb.n = 0;
+  __syncwarp();
+}
+
 // All 32 lanes call. Lanes with `want` contend for (node, cell) = key. Lanes
 // with equal keys are merged first and only the lowest gidx goes to the
-// table. Keys that are new in this update are appended to the backlog (one
-// atomic per warp) and get a voxel slot of their node (one atomic per node
-// and warp).
-__device__ __forceinline__ void warp_claim(const Ctx& c, bool want, unsigned long long key,
-                                           uint32_t gidx, uint32_t rgba, uint32_t node) {
+// table. A key new in this update is staged for the backlog and counted
+// towards its node's new voxels (a reduction: no value comes back).
+__device__ __forceinline__ void warp_claim(const Ctx& c, WarpBuf& wb, bool want,
+                                           unsigned long long key, uint32_t gidx, uint32_t rgba,
+                                           uint32_t node) {
   const uint32_t lane = lane_id();
   const unsigned m = __ballot_sync(FULL_MASK, want);
   if (m == 0u) return;
@@ -349,35 +386,39 @@ __device__ __forceinline__ void warp_claim(const Ctx& c, bool want, unsigned lon
   }
   const unsigned mi = __ballot_sync(FULL_MASK, inst);
   if (mi == 0u) return;
-  const int leader = __ffs(mi) - 1;
-  uint32_t e0 = 0;
-  if ((int)lane == leader) e0 = atomicAdd(&c.ctl->nkeys, (uint32_t)__popc(mi));
-  e0 = __shfl_sync(FULL_MASK, e0, leader);
+  const uint32_t ni = (uint32_t)__popc(mi);
+  if (wb.n + ni > WBUF) warp_flush(c, wb);
   if (inst) {
-    const uint32_t below = (1u << lane) - 1u;
-    const uint32_t e = e0 + __popc(mi & below);
+    wb.buf[wb.n + __popc(mi & ((1u << lane) - 1u))] = h;
     const unsigned gm = __match_any_sync(mi, node);
-    const int nl = __ffs(gm) - 1;
-    uint32_t t0 = 0;
-    if ((int)lane == nl) t0 = c.num[node] + atomicAdd(&c.cnt[node], (uint32_t)__popc(gm));
-    t0 = __shfl_sync(gm, t0, nl);
-    if (e < c.backlog_cap) c.keys[e] = make_uint2(h, t0 + __popc(gm & below));
-    else set_error(c, E_BACKLOG);
+    if ((int)lane == __ffs(gm) - 1) atomicAdd(&c.cnt[node], (uint32_t)__popc(gm));
+  }
+  wb.n += ni;
+}
+
+// All 32 lanes call. Lanes with `valid` count one point into `leaf` (a
+// reduction per distinct leaf of the warp; the slot is given at store).
+__device__ __forceinline__ void warp_tally(const Ctx& c, bool valid, uint32_t leaf) {
+  const unsigned m = __ballot_sync(FULL_MASK, valid);
+  if (valid) {
+    const unsigned grp = __match_any_sync(m, leaf);
+    if ((int)lane_id() == __ffs(grp) - 1) atomicAdd(&c.cnt[leaf], (uint32_t)__popc(grp));
   }
 }
 
-// All 32 lanes call. Lanes with `valid` count one point into `leaf` and get
-// their slot there: stored points + their rank among this update's points.
-__device__ __forceinline__ uint32_t warp_count(const Ctx& c, bool valid, uint32_t leaf) {
+// All 32 lanes call. Lanes with `valid` take the next free slot of `node`
+// in this update: its stored count before the update + a running cursor.
+__device__ __forceinline__ uint32_t warp_slot(const Ctx& c, bool valid, uint32_t node) {
   const uint32_t lane = lane_id();
-  unsigned m = __ballot_sync(FULL_MASK, valid);
+  const unsigned m = __ballot_sync(FULL_MASK, valid);
   uint32_t base = 0, rank = 0;
   int leader = 0;
   if (valid) {
-    unsigned grp = __match_any_sync(m, leaf);
+    const unsigned grp = __match_any_sync(m, node);
     leader = __ffs(grp) - 1;
     rank = __popc(grp & ((1u << lane) - 1u));
-    if ((int)lane == leader) base = c.num[leaf] + atomicAdd(&c.cnt[leaf], (uint32_t)__popc(grp));
+    if ((int)lane == leader)
+      base = c.meta[node].st_base + atomicAdd(&c.scur[node], (uint32_t)__popc(grp));
   }
   base = __shfl_sync(FULL_MASK, base, leader);
   return base + rank;
@@ -386,11 +427,12 @@ __device__ __forceinline__ uint32_t warp_count(const Ctx& c, bool valid, uint32_
 // ------------------------------------------------------------ phase: count1
 
 // Iteration 1 for the batch points [0, n): descend, claim, count. `smem`
-// holds NODE_CACHE_BYTES of dynamic shared memory; n_nodes is the node count.
+// holds PHASE_SMEM_BYTES of dynamic shared memory; n_nodes is the node count.
 __device__ void phase_count1(const Ctx& c, uint32_t* smem, uint32_t n_nodes, const int4* pts,
                              uint64_t n, unsigned long long base, uint64_t warp0,
                              uint64_t nwarps) {
   const NodeCache nc = load_node_cache(c, smem, n_nodes);
+  WarpBuf wb = warp_buf(smem);
   const uint32_t lane = lane_id();
   for (uint64_t w = warp0; w * 32 < n; w += nwarps) {
     uint64_t i = w * 32 + lane;
@@ -440,16 +482,14 @@ __device__ void phase_count1(const Ctx& c, uint32_t* smem, uint32_t n_nodes, con
 #pragma unroll
       for (int k = 0; k < DESCENT_GROUP; ++k) {
         const bool want = ginner[k] && ((gword[k] >> (gcell[k] & 31u)) & 1u) == 0u;
-        warp_claim(c, want, ((unsigned long long)gnode[k] << (3u * c.G)) | gcell[k], gidx,
+        warp_claim(c, wb, want, ((unsigned long long)gnode[k] << (3u * c.G)) | gcell[k], gidx,
                    (uint32_t)p.w, gnode[k]);
       }
     }
-    uint32_t slot = warp_count(c, valid, node);
-    if (valid) {
-      c.b_cur[i] = node;
-      c.b_slot[i] = slot;
-    }
+    warp_tally(c, valid, node);
+    if (valid) c.b_cur[i] = node;
   }
+  warp_flush(c, wb);
 }
 
 // ----------------------------------------------------------- phase: advance
@@ -457,10 +497,9 @@ __device__ void phase_count1(const Ctx& c, uint32_t* smem, uint32_t n_nodes, con
 // One item whose cursor node may have split in the previous round: if so it
 // samples that node's grid (empty until store, so every point contends) and
 // moves one level down, counting into the child. Returns true when it moved;
-// cur and slot then hold the new cursor and slot.
-__device__ __forceinline__ bool advance_item(const Ctx& c, NodeCache nc, bool valid,
-                                             int4 p, uint32_t gidx, uint32_t& cur,
-                                             uint32_t& slot) {
+// cur then holds the new cursor.
+__device__ __forceinline__ bool advance_item(const Ctx& c, NodeCache nc, WarpBuf& wb, bool valid,
+                                             int4 p, uint32_t gidx, uint32_t& cur) {
   const uint32_t node = cur;
   const bool in_range = node < c.max_nodes;
   if (valid && !in_range) set_error(c, E_INTERNAL);
@@ -473,13 +512,10 @@ __device__ __forceinline__ bool advance_item(const Ctx& c, NodeCache nc, bool va
     cell = cell_index(rx, ry, rz, L, c.G);
     nxt = ch + octant(rx, ry, rz, L);
   }
-  warp_claim(c, moving, ((unsigned long long)node << (3u * c.G)) | cell, gidx, (uint32_t)p.w,
+  warp_claim(c, wb, moving, ((unsigned long long)node << (3u * c.G)) | cell, gidx, (uint32_t)p.w,
              node);
-  const uint32_t s = warp_count(c, moving, nxt);
-  if (moving) {
-    cur = nxt;
-    slot = s;
-  }
+  warp_tally(c, moving, nxt);
+  if (moving) cur = nxt;
   return moving;
 }
 
@@ -491,6 +527,7 @@ __device__ void phase_advance(const Ctx& c, uint32_t* smem, uint32_t n_nodes, co
                               uint64_t n, unsigned long long base, uint32_t t_lo, uint32_t t_hi,
                               uint32_t s_lo, uint32_t s_hi, uint64_t warp0, uint64_t nwarps) {
   const NodeCache nc = load_node_cache(c, smem, n_nodes);
+  WarpBuf wb = warp_buf(smem);
   const uint32_t lane = lane_id();
   const uint32_t zpg = (c.grid_bytes + ZERO_UNIT - 1) / ZERO_UNIT;  // zero units per grid
   const uint32_t parts = (c.C + TASK_PART - 1) / TASK_PART;       // units per task
@@ -512,12 +549,11 @@ __device__ void phase_advance(const Ctx& c, uint32_t* smem, uint32_t n_nodes, co
     } else if (w < uz + ub) {
       const uint64_t i = (w - uz) * 32 + lane;
       const bool valid = i < n;
-      const int4 p = valid ? __ldg(pts + i) : make_int4(0, 0, 0, 0);
-      uint32_t cur = valid ? c.b_cur[i] : 0u, slot = 0;
-      if (advance_item(c, nc, valid, p, (uint32_t)(base + i), cur, slot)) {
-        c.b_cur[i] = cur;
-        c.b_slot[i] = slot;
-      }
+      uint32_t cur = valid ? c.b_cur[i] : 0u;
+      // read the point only when its cursor node split (it moves)
+      const bool may_move = valid && cur < c.max_nodes && node_child(c, nc, cur) != NONE;
+      const int4 p = may_move ? __ldg(pts + i) : make_int4(0, 0, 0, 0);
+      if (advance_item(c, nc, wb, valid, p, (uint32_t)(base + i), cur)) c.b_cur[i] = cur;
     } else {
       const uint64_t u = w - uz - ub;
       const uint32_t t = (uint32_t)(u / parts), part = (uint32_t)(u % parts);
@@ -534,19 +570,17 @@ __device__ void phase_advance(const Ctx& c, uint32_t* smem, uint32_t n_nodes, co
         const uint32_t q = q0 + lane;
         const bool valid = q < q_end;
         const uint32_t e = tk.dst + q;
-        uint32_t cur = valid ? (fresh ? tk.node : c.sp_cur[e]) : 0u, slot = 0;
+        uint32_t cur = valid ? (fresh ? tk.node : c.sp_cur[e]) : 0u;
         // read the point only when its cursor node split (it moves)
         const uint32_t ch = (valid && cur < c.max_nodes) ? node_child(c, nc, cur) : NONE;
         const bool may_move = ch != NONE;
         const int4 p = may_move ? chunk_recs(c, tk.ref)[q] : make_int4(0, 0, 0, 0);
         const uint32_t g = may_move ? chunk_aux(c, tk.ref)[q] : 0u;
-        if (advance_item(c, nc, valid, p, g, cur, slot)) {
-          c.sp_cur[e] = cur;
-          c.sp_slot[e] = slot;
-        }
+        if (advance_item(c, nc, wb, valid, p, g, cur)) c.sp_cur[e] = cur;
       }
     }
   }
+  warp_flush(c, wb);
 }
 
 // ------------------------------------------------------------ phase: decide
@@ -572,6 +606,8 @@ __device__ void alloc_chunks(const Ctx& c, uint32_t id, uint32_t total, bool lea
   m.st_nch = have;
   m.st_tail = m.tail;
   m.st_seq = 0;
+  m.st_base = c.num[id];
+  c.scur[id] = 0;
   if (need <= have) return;
   const uint32_t k = need - have;
   const uint32_t seq = atomicAdd(&c.ctl->alloc_seq, k);
@@ -638,7 +674,8 @@ __device__ void split_leaf(const Ctx& c, uint32_t id) {
     cm.st_nch = 0;
     cm.st_tail = NONE;
     cm.st_seq = 0;
-    for (int q = 0; q < 5; ++q) cm.pad[q] = 0;
+    cm.st_base = 0;
+    for (int q = 0; q < 4; ++q) cm.pad[q] = 0;
     c.meta[c0 + k] = cm;
     c.child[c0 + k] = NONE;
     c.gridref[c0 + k] = NONE;
@@ -716,7 +753,7 @@ __device__ void phase_rollback(const Ctx& c, uint32_t n_nodes, uint64_t t0, uint
   for (uint64_t t = t0; t < n_nodes; t += nthreads) c.cnt[t] = 0;
   const uint32_t nk = min(*reinterpret_cast<volatile unsigned int*>(&c.ctl->nkeys), c.backlog_cap);
   for (uint64_t t = t0; t < nk; t += nthreads) {
-    HSlot* s = c.hash + c.keys[t].x;
+    HSlot* s = c.hash + c.keys[t];
     s->key = HASH_EMPTY;
     s->val = HASH_EMPTY;
   }
@@ -748,36 +785,55 @@ __device__ __forceinline__ void store_rec(const Ctx& c, uint32_t node, uint32_t 
 }
 
 // Store the batch points, the re-inserted points of the spill tasks [0,
-// n_tasks) and the n_keys new voxels; hand the chunks of split leaves (one
-// per task) to the pool above pool_top (the caller then raises pool_top).
+// n_tasks) and the n_keys new voxels, each at the next free slot of its node;
+// hand the chunks of split leaves (one per task) to the pool above pool_top
+// (the caller then raises pool_top). Loops are warp-uniform so that the
+// lanes of a warp share one slot reservation per node.
 __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned long long base,
                             uint32_t n_tasks, uint32_t n_keys, int pool_top, uint64_t t0,
                             uint64_t nthreads) {
-  for (uint64_t i = t0; i < n; i += nthreads)
-    store_rec(c, c.b_cur[i], c.b_slot[i], __ldg(pts + i), (uint32_t)(base + i));
+  const uint32_t lane = lane_id();
+  const uint64_t w0 = t0 - lane, wstride = nthreads;  // warp-aligned start and stride
+  for (uint64_t b0 = w0; b0 < n; b0 += wstride) {
+    const uint64_t i = b0 + lane;
+    const bool valid = i < n;
+    const uint32_t node = valid ? c.b_cur[i] : 0u;
+    const bool ok = valid && node < c.max_nodes;
+    if (valid && !ok) set_error(c, E_INTERNAL);
+    const uint32_t slot = warp_slot(c, ok, node);
+    if (ok) store_rec(c, node, slot, __ldg(pts + i), (uint32_t)(base + i));
+  }
   const uint64_t tp = (uint64_t)n_tasks * c.C;
-  for (uint64_t u = t0; u < tp; u += nthreads) {
-    const uint32_t t = (uint32_t)(u / c.C), q = (uint32_t)(u - (uint64_t)t * c.C);
-    const SpillTask tk = c.tasks[t];
-    if (q >= tk.n) continue;
-    if (!ref_ok(c, tk.ref, c.chunk_bytes) || (unsigned long long)tk.dst + tk.n > c.spill_cap) {
+  for (uint64_t b0 = w0; b0 < tp; b0 += wstride) {
+    const uint64_t u = b0 + lane;
+    bool valid = u < tp;
+    const uint32_t t = valid ? (uint32_t)(u / c.C) : 0u;
+    const uint32_t q = valid ? (uint32_t)(u - (uint64_t)t * c.C) : 0u;
+    SpillTask tk = valid ? c.tasks[t] : SpillTask{NONE, 0, 0, 0};
+    valid = valid && q < tk.n;
+    if (valid && (!ref_ok(c, tk.ref, c.chunk_bytes) ||
+                  (unsigned long long)tk.dst + tk.n > c.spill_cap)) {
       set_error(c, E_INTERNAL);
-      continue;
+      valid = false;
     }
-    const uint32_t e = tk.dst + q;
-    store_rec(c, c.sp_cur[e], c.sp_slot[e], chunk_recs(c, tk.ref)[q], chunk_aux(c, tk.ref)[q]);
+    const uint32_t node = valid ? c.sp_cur[tk.dst + q] : 0u;
+    const bool ok = valid && node < c.max_nodes;
+    if (valid && !ok) set_error(c, E_INTERNAL);
+    const uint32_t slot = warp_slot(c, ok, node);
+    if (ok) store_rec(c, node, slot, chunk_recs(c, tk.ref)[q], chunk_aux(c, tk.ref)[q]);
   }
   const uint32_t G = c.G, cmask = (1u << (3u * G)) - 1u, amask = (1u << G) - 1u;
-  for (uint64_t e = t0; e < n_keys; e += nthreads) {
-    const uint2 k = c.keys[e];
-    HSlot* s = c.hash + k.x;
-    const unsigned long long key = s->key, val = s->val;
+  for (uint64_t b0 = w0; b0 < n_keys; b0 += wstride) {
+    const uint64_t e = b0 + lane;
+    const bool valid = e < n_keys;
+    HSlot* s = valid ? c.hash + c.keys[e] : nullptr;
+    const unsigned long long key = valid ? s->key : 0ull, val = valid ? s->val : 0ull;
     const uint32_t node = (uint32_t)(key >> (3u * G)), cell = (uint32_t)key & cmask;
-    const uint32_t gref = node < c.max_nodes ? c.gridref[node] : NONE;
-    if (!ref_ok(c, gref, c.grid_bytes)) {
-      set_error(c, E_INTERNAL);
-      continue;
-    }
+    const uint32_t gref = (valid && node < c.max_nodes) ? c.gridref[node] : NONE;
+    const bool ok = valid && ref_ok(c, gref, c.grid_bytes);
+    if (valid && !ok) set_error(c, E_INTERNAL);
+    const uint32_t slot = warp_slot(c, ok, node);
+    if (!ok) continue;
     const NodeMeta& m = c.meta[node];
     const uint32_t L = c.rlog2 - m.level;
     const uint32_t cx = cell & amask, cy = (cell >> G) & amask, cz = cell >> (2u * G);
@@ -787,7 +843,7 @@ __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned 
     v.y = m.min[1] + (int32_t)(((2ull * cy + 1ull) << L) >> (G + 1u));
     v.z = m.min[2] + (int32_t)(((2ull * cz + 1ull) << L) >> (G + 1u));
     v.w = (int32_t)(uint32_t)val;
-    store_rec(c, node, k.y, v, cell);
+    store_rec(c, node, slot, v, cell);
     atomicOr(grid_words(c, gref) + (cell >> 5), 1u << (cell & 31u));
     s->key = HASH_EMPTY;
     s->val = HASH_EMPTY;

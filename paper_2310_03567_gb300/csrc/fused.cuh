@@ -88,6 +88,20 @@ __device__ __forceinline__ bool grid_barrier(const Ctx& c, FusedCtl* f) {
   return s_ok != 0;
 }
 
+// Phase clock (block 0, thread 0): charge the time since the previous tick
+// to `phase`. Called right after a barrier, so it covers the phase and the
+// barrier that closed it.
+struct PhaseClock {
+  unsigned long long t;
+  __device__ __forceinline__ void tick(const Ctx& c, int phase) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      const unsigned long long now = globaltimer_ns();
+      atomicAdd(&c.ctl->phase_ns[phase], now - t);
+      t = now;
+    }
+  }
+};
+
 // All batches of `batches`, in order, each one complete update. Before a
 // batch other than the first, stop once more than budget_ns has passed since
 // the launch began (Section 7.2's frame budget; batches are never cut);
@@ -100,7 +114,8 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t warp0 = tid / 32, nwarps = nthreads / 32;
   const unsigned long long t_begin = globaltimer_ns();
-  extern __shared__ uint32_t smem[];  // node-table cache (NODE_CACHE_BYTES)
+  extern __shared__ uint32_t smem[];  // node-table cache (PHASE_SMEM_BYTES)
+  PhaseClock clk{t_begin};
   for (uint32_t b = 0; b < n_batches; ++b) {
     // every value read here was written before the last barrier and is not
     // written again before the next one, so all threads decide alike
@@ -112,10 +127,12 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
     if (bd.n) {
       phase_count1(c, smem, nodes0, bd.pts, bd.n, base, warp0, nwarps);
       if (!grid_barrier(c, f)) return;
+      clk.tick(c, PH_COUNT);
       rejected = vload(&c.ctl->reject) != 0u;  // set only by the count round
       if (rejected) {
         phase_rollback(c, nodes0, tid, nthreads);
         if (!grid_barrier(c, f)) return;  // all have read the flag before it is cleared
+        clk.tick(c, PH_ROLLBACK);
         if (tid == 0) {
           phase_end_rejected(c);
           c.ctl->st_rejected_async += 1;
@@ -128,6 +145,7 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
         for (;;) {
           phase_decide(c, s_lo, s_hi, n_lo, n_hi, tid, nthreads);
           if (!grid_barrier(c, f)) return;
+          clk.tick(c, PH_DECIDE);
           const uint32_t sc = vload(&c.ctl->split_count), nn = vload(&c.ctl->n_nodes);
           const uint32_t nt = vload(&c.ctl->ntasks);
           if (sc == s_hi) break;
@@ -144,12 +162,14 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
           ++iters;
           phase_advance(c, smem, nn, bd.pts, bd.n, base, t_lo, t_hi, s_lo, s_hi, warp0, nwarps);
           if (!grid_barrier(c, f)) return;
+          clk.tick(c, PH_ADVANCE);
         }
         const uint32_t n_tasks = vload(&c.ctl->ntasks);
         const uint32_t n_keys = min(vload(&c.ctl->nkeys), c.backlog_cap);
         const int pool_top = vload(&c.ctl->pool_top);
         phase_store(c, bd.pts, bd.n, base, n_tasks, n_keys, pool_top, tid, nthreads);
         if (!grid_barrier(c, f)) return;
+        clk.tick(c, PH_STORE);
         if (tid == 0) phase_end(c, bd.n, iters);
       }
     }
@@ -158,7 +178,10 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
       if (budget_ns != NO_BUDGET && globaltimer_ns() - t_begin > budget_ns) f->stop = 1;
     }
     if (!grid_barrier(c, f)) return;
+    clk.tick(c, PH_END);
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(&c.ctl->phase_ns[PH_LAUNCH], globaltimer_ns() - t_begin);
 }
 
 }  // namespace sl

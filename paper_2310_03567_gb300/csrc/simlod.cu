@@ -24,7 +24,10 @@ constexpr int PBLOCK = PHASE_BLOCK;  // count / advance kernels (one node-table 
 __global__ void k_init(Ctx c) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Ctl* t = c.ctl;
+    unsigned long long phase_ns[8];  // diagnostics survive a reset
+    for (int k = 0; k < 8; ++k) phase_ns[k] = t->phase_ns[k];
     memset(t, 0, sizeof(Ctl));
+    for (int k = 0; k < 8; ++k) t->phase_ns[k] = phase_ns[k];
     t->n_nodes = 1;
     t->bump = c.dir_bytes;  // the root's chunk directory is the first data ref
     NodeMeta m;
@@ -105,7 +108,7 @@ static const char* const kKernelNames[SIMLOD_N_KERNELS] = {
 
 struct Layout {
   size_t ctl, fctl, batches, child, gridref, cnt, num, meta, pool, pending, alloc_refs, splits,
-      tasks, sp_cur, sp_slot, b_cur, b_slot, hash, keys, staging, data, end;
+      tasks, sp_cur, b_cur, scur, hash, keys, staging, data, end;
   uint64_t hash_slots, max_chunks, max_splits, data_bytes;
 };
 
@@ -140,6 +143,7 @@ struct simlod {
   std::vector<Pending> pending;
   uint64_t launches[SIMLOD_N_KERNELS];
   double ms[SIMLOD_N_KERNELS];
+  unsigned long long phase_ns_cleared[SIMLOD_N_PHASES];
 };
 
 namespace {
@@ -212,11 +216,10 @@ bool plan_layout(const simlod_config* c, size_t arena_bytes, Layout* L) {
   L->meta = take(sizeof(NodeMeta) * N);
   L->splits = take(sizeof(SplitEntry) * L->max_splits);
   L->sp_cur = take(4 * S);
-  L->sp_slot = take(4 * S);
   L->b_cur = take(4 * B);
-  L->b_slot = take(4 * B);
+  L->scur = take(4 * N);
   L->hash = take(sizeof(HSlot) * L->hash_slots);
-  L->keys = take(sizeof(uint2) * c->backlog_capacity);
+  L->keys = take(sizeof(uint32_t) * c->backlog_capacity);
   L->staging = take(16 * B);
   const size_t fixed = align_up(o, 256);
   if (arena_bytes < fixed) return false;
@@ -255,11 +258,10 @@ void make_ctx(simlod_t* h) {
   c.splits = reinterpret_cast<SplitEntry*>(a + L.splits);
   c.tasks = reinterpret_cast<SpillTask*>(a + L.tasks);
   c.sp_cur = reinterpret_cast<uint32_t*>(a + L.sp_cur);
-  c.sp_slot = reinterpret_cast<uint32_t*>(a + L.sp_slot);
   c.b_cur = reinterpret_cast<uint32_t*>(a + L.b_cur);
-  c.b_slot = reinterpret_cast<uint32_t*>(a + L.b_slot);
+  c.scur = reinterpret_cast<uint32_t*>(a + L.scur);
   c.hash = reinterpret_cast<HSlot*>(a + L.hash);
-  c.keys = reinterpret_cast<uint2*>(a + L.keys);
+  c.keys = reinterpret_cast<uint32_t*>(a + L.keys);
   c.staging = reinterpret_cast<int4*>(a + L.staging);
   c.data = a + L.data;
   c.data_bytes = L.data_bytes;
@@ -377,7 +379,7 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
   const unsigned gp = std::max(1u, std::min<unsigned>(grid_for(h, n, PBLOCK), (unsigned)PHASE_MIN_BLOCKS * h->sm_count));
   int rc;
   rc = launch(h, K_COUNT, s, [&] {
-    k_count1<<<gp, PBLOCK, NODE_CACHE_BYTES, s>>>(c, pts, n, base, nodes0);
+    k_count1<<<gp, PBLOCK, PHASE_SMEM_BYTES, s>>>(c, pts, n, base, nodes0);
   });
   if (rc) return poison(h, rc);
   rc = launch(h, K_DECIDE, s, [&] {
@@ -405,7 +407,7 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
         std::max(1u, std::min<unsigned>(grid_for(h, units * 32, PBLOCK), (unsigned)PHASE_MIN_BLOCKS * h->sm_count));
     const uint32_t nn = n_hi;
     rc = launch(h, K_ADVANCE, s, [&] {
-      k_advance<<<ga, PBLOCK, NODE_CACHE_BYTES, s>>>(c, pts, n, base, nn, t_lo, t_hi, s_lo, s_hi);
+      k_advance<<<ga, PBLOCK, PHASE_SMEM_BYTES, s>>>(c, pts, n, base, nn, t_lo, t_hi, s_lo, s_hi);
     });
     if (rc) return poison(h, rc);
     const uint64_t cand = (uint64_t)(s_hi - s_lo) + (n_hi - n_lo);
@@ -469,7 +471,7 @@ int launch_fused(simlod_t* h, const simlod_point* const* d_batches, const uint64
   cudaError_t le = cudaSuccess;
   int rc = launch(h, K_FUSED, s, [&] {
     le = cudaLaunchCooperativeKernel((const void*)k_fused, dim3(h->fused_grid),
-                                     dim3(FUSED_BLOCK), args, NODE_CACHE_BYTES, s);
+                                     dim3(FUSED_BLOCK), args, PHASE_SMEM_BYTES, s);
   });
   if (rc || le != cudaSuccess) return poison(h, SIMLOD_ERR_CUDA);
   h->base += total;  // upper bound until the next control-block read
@@ -568,11 +570,11 @@ SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t are
   }
   memset(h->ctl_host, 0, sizeof(Ctl));
   if (cudaFuncSetAttribute(k_count1, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           NODE_CACHE_BYTES) != cudaSuccess ||
+                           PHASE_SMEM_BYTES) != cudaSuccess ||
       cudaFuncSetAttribute(k_advance, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           NODE_CACHE_BYTES) != cudaSuccess ||
+                           PHASE_SMEM_BYTES) != cudaSuccess ||
       cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           NODE_CACHE_BYTES) != cudaSuccess) {
+                           PHASE_SMEM_BYTES) != cudaSuccess) {
     cudaFreeHost(h->ctl_host);
     delete h;
     return SIMLOD_ERR_CUDA;
@@ -580,12 +582,18 @@ SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t are
   int coop = 0, bpsm = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_fused, FUSED_BLOCK,
-                                                             NODE_CACHE_BYTES) == cudaSuccess)
+                                                             PHASE_SMEM_BYTES) == cudaSuccess)
     h->fused_grid = std::min(bpsm, 4) * h->sm_count;
   if (cudaMallocHost(reinterpret_cast<void**>(&h->desc_host),
                      sizeof(BatchDesc) * MAX_FUSED_BATCHES) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&h->fctl_host), sizeof(FusedCtl)) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->desc_done, cudaEventDisableTiming) != cudaSuccess) {
+    simlod_destroy(h);
+    return SIMLOD_ERR_CUDA;
+  }
+  // the arena is the caller's memory: start from a zeroed control block
+  if (cudaMemsetAsync(h->ctx.ctl, 0, sizeof(Ctl), static_cast<cudaStream_t>(stream)) !=
+      cudaSuccess) {
     simlod_destroy(h);
     return SIMLOD_ERR_CUDA;
   }
@@ -800,6 +808,8 @@ SIMLOD_API int simlod_set_timing(simlod_t* h, int enable, int clear) {
     harvest_timing(h);
     memset(h->launches, 0, sizeof(h->launches));
     memset(h->ms, 0, sizeof(h->ms));
+    if (read_ctl(h, h->last_stream) == SIMLOD_OK)
+      for (int k = 0; k < SIMLOD_N_PHASES; ++k) h->phase_ns_cleared[k] = h->ctl_host->phase_ns[k];
   }
   h->timing = enable != 0;
   return SIMLOD_OK;
@@ -813,6 +823,14 @@ SIMLOD_API int simlod_get_timing(simlod_t* h, simlod_timing* out) {
     out->name[k] = kKernelNames[k];
     out->launches[k] = h->launches[k];
     out->ms[k] = h->ms[k];
+  }
+  static const char* const kPhaseNames[SIMLOD_N_PHASES] = {
+      "count", "decide", "advance", "store", "end", "rollback", "launch", "other"};
+  int rc = read_ctl(h, h->last_stream);
+  if (rc) return rc;
+  for (int k = 0; k < SIMLOD_N_PHASES; ++k) {
+    out->phase_name[k] = kPhaseNames[k];
+    out->phase_ms[k] = (h->ctl_host->phase_ns[k] - h->phase_ns_cleared[k]) * 1e-6;
   }
   return SIMLOD_OK;
 }

@@ -75,9 +75,14 @@ class Stats(ctypes.Structure):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
+N_PHASES = 8
+
+
 class Timing(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p * N_KERNELS), ("launches", ctypes.c_uint64 * N_KERNELS),
-                ("ms", ctypes.c_double * N_KERNELS)]
+                ("ms", ctypes.c_double * N_KERNELS),
+                ("phase_name", ctypes.c_char_p * N_PHASES),
+                ("phase_ms", ctypes.c_double * N_PHASES)]
 
 
 # numpy views of the snapshot records (same layout as the C structs)
@@ -318,6 +323,14 @@ class Octree:
         if rc != OK:
             raise SimlodError(rc, "simlod_get_timing")
         return {t.name[k].decode(): (int(t.launches[k]), float(t.ms[k])) for k in range(N_KERNELS)}
+
+    def phase_times(self) -> dict:
+        """Milliseconds the fused form spent per phase since the last clear."""
+        t = Timing()
+        rc = self._lib.simlod_get_timing(self._h, ctypes.byref(t))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_get_timing")
+        return {t.phase_name[k].decode(): float(t.phase_ms[k]) for k in range(N_PHASES)}
 
     def snapshot(self) -> Snapshot:
         s = Snapshot_t()
