@@ -36,6 +36,7 @@
 // count / advance pass; the node ids of the upper levels are the smallest.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 
 #include "simlod.h"
@@ -53,20 +54,25 @@ constexpr uint32_t CHUNK_HEADER = 16;
 #define SL_NODE_CACHE 8192
 #endif
 #ifndef SL_DESCENT_GROUP
-#define SL_DESCENT_GROUP 4
+#define SL_DESCENT_GROUP 2
 #endif
 #ifndef SL_PHASE_BLOCK
 #define SL_PHASE_BLOCK 512
 #endif
 #ifndef SL_PHASE_MIN_BLOCKS
-#define SL_PHASE_MIN_BLOCKS 3
+#define SL_PHASE_MIN_BLOCKS 2
 #endif
-#ifndef SL_CAS128
-#define SL_CAS128 0
+#ifndef SL_STORE_UNROLL
+#define SL_STORE_UNROLL 2
+#endif
+#ifndef SL_ADVANCE_UNROLL
+#define SL_ADVANCE_UNROLL 1
+#endif
+#ifndef SL_CLAIM_READ_VAL
+#define SL_CLAIM_READ_VAL 0
 #endif
 constexpr uint32_t NODE_CACHE = SL_NODE_CACHE;         // nodes mirrored in shared memory
 constexpr uint32_t NODE_CACHE_BYTES = NODE_CACHE * 8;  // child + grid reference
-constexpr uint32_t TASK_PART = 128;                    // points of a spill task per warp unit
 constexpr uint32_t ZERO_UNIT = 4096;                   // bytes of grid zeroed per warp unit
 constexpr int DESCENT_GROUP = SL_DESCENT_GROUP;        // levels whose grid words load together
 constexpr uint32_t WBUF = 64;                          // new-cell slots staged per warp
@@ -129,6 +135,8 @@ struct NodeMeta {
   uint32_t pad[4];
 };
 static_assert(sizeof(NodeMeta) == 64, "NodeMeta size");
+static_assert(offsetof(NodeMeta, st_nch) == 32 && offsetof(NodeMeta, st_base) == 44,
+              "the store map is one aligned 16-byte load");
 
 struct __align__(16) HSlot {
   unsigned long long key;  // (node << 3G) | cell, HASH_EMPTY when free
@@ -290,53 +298,45 @@ __device__ __forceinline__ uint32_t node_grid(const Ctx& c, NodeCache nc, uint32
 
 // -------------------------------------------------------- voxel claims
 
-// Offer val = (gidx << 32 | rgba) as the colour of cell `key`; the lowest
-// gidx wins. Returns true, with the table slot in h, when this call put the
-// key into the table (the cell is new in this update). A free slot takes key
-// and value in one 16-byte compare-and-swap; a slot holding the key is
-// lowered with atomicMin only when this value is smaller.
-__device__ __forceinline__ bool hash_claim(const Ctx& c, unsigned long long key,
-                                           unsigned long long val, uint32_t& h) {
-  h = (uint32_t)fmix64(key) & c.hash_mask;
-#if SL_CAS128
-  HSlot empty, mine;
-  empty.key = HASH_EMPTY;
-  empty.val = HASH_EMPTY;
-  mine.key = key;
-  mine.val = val;
-  for (int probe = 0; probe < MAX_PROBES; ++probe) {
-    HSlot* s = c.hash + h;
-    const HSlot old = atomicCAS(s, empty, mine);
-    if (old.key == HASH_EMPTY) return true;
-    if (old.key == key) {
-      if (old.val > val) atomicMin(&s->val, val);
-      return false;
-    }
-    h = (h + 1u) & c.hash_mask;
-  }
+template <typename T>
+__device__ __forceinline__ T vload(const T* p) {
+  return *reinterpret_cast<const volatile T*>(p);
+}
+
+// Lower the colour of a cell in the table to val (gidx << 32 | rgba) if val
+// is smaller. The result is not used, so the GPU does not wait for it.
+__device__ __forceinline__ void hash_lower(HSlot* s, unsigned long long val) {
+#if SL_CLAIM_READ_VAL
+  if (vload(&s->val) > val) atomicMin(&s->val, val);
 #else
-  for (int probe = 0; probe < MAX_PROBES; ++probe) {
+  atomicMin(&s->val, val);
+#endif
+}
+
+// Probes after the first for `key` (slot h held another key): returns true,
+// with the slot in h, when this call put the key into the table (the cell is
+// new in this update); a slot already holding the key is lowered to val.
+__device__ bool hash_claim_rest(const Ctx& c, unsigned long long key, unsigned long long val,
+                                uint32_t& h) {
+  for (int probe = 1; probe < MAX_PROBES; ++probe) {
+    h = (h + 1u) & c.hash_mask;
     HSlot* s = c.hash + h;
-    unsigned long long k = *reinterpret_cast<volatile unsigned long long*>(&s->key);
+    unsigned long long k = vload(&s->key);
     if (k == HASH_EMPTY) {
-      const unsigned long long old = atomicCAS(&s->key, HASH_EMPTY, key);
-      if (old == HASH_EMPTY) {
+      k = atomicCAS(&s->key, HASH_EMPTY, key);
+      if (k == HASH_EMPTY) {
         atomicMin(&s->val, val);
         return true;
       }
-      k = old;
     }
     if (k == key) {
-      if (*reinterpret_cast<volatile unsigned long long*>(&s->val) > val) atomicMin(&s->val, val);
+      hash_lower(s, val);
       return false;
     }
-    h = (h + 1u) & c.hash_mask;
   }
-#endif
   set_error(c, E_BACKLOG);
   return false;
 }
-
 // Per-warp staging of the table slots of new cells (shared memory), flushed
 // to the backlog with one atomic per flush.
 struct WarpBuf {
@@ -367,33 +367,73 @@ __device__ __forceinline__ void warp_flush(const Ctx& c, WarpBuf& wb) {
   __syncwarp();
 }
 
-// All 32 lanes call. Lanes with `want` contend for (node, cell) = key. Lanes
-// with equal keys are merged first and only the lowest gidx goes to the
-// table. A key new in this update is staged for the backlog and counted
-// towards its node's new voxels (a reduction: no value comes back).
-__device__ __forceinline__ void warp_claim(const Ctx& c, WarpBuf& wb, bool want,
-                                           unsigned long long key, uint32_t gidx, uint32_t rgba,
-                                           uint32_t node) {
+// All 32 lanes call. For each of N levels j, lanes with want[j] contend for
+// the cell key[j] = (node[j], cell) with val = (gidx << 32 | rgba); the lowest
+// gidx wins. Lanes with equal keys are merged first and only the lowest gidx
+// goes to the table. The first probes of all N levels are issued together
+// (their key loads, then their compare-and-swaps), so a descent pays about
+// two L2 round trips for all its claims. A key new in this update is staged
+// for the backlog and counted towards its node's new voxels.
+template <int N>
+__device__ __forceinline__ void warp_claim(const Ctx& c, WarpBuf& wb, const bool (&want)[N],
+                                           const unsigned long long (&key)[N],
+                                           const uint32_t (&gidx)[N], const uint32_t (&rgba)[N],
+                                           const uint32_t (&node)[N]) {
   const uint32_t lane = lane_id();
-  const unsigned m = __ballot_sync(FULL_MASK, want);
-  if (m == 0u) return;
-  bool inst = false;
-  uint32_t h = 0;
-  if (want) {
-    const unsigned grp = __match_any_sync(m, key);
-    const unsigned best = __reduce_min_sync(grp, gidx);
-    if (gidx == best) inst = hash_claim(c, key, ((unsigned long long)gidx << 32) | rgba, h);
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < N; ++j) any = any || want[j];
+  if (__ballot_sync(FULL_MASK, any) == 0u) return;
+  bool lead[N], cas[N], inst[N];
+  uint32_t h[N];
+  unsigned long long k0[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const unsigned m = __ballot_sync(FULL_MASK, want[j]);
+    lead[j] = false;
+    if (want[j]) {
+      const unsigned grp = __match_any_sync(m, key[j]);
+      lead[j] = __reduce_min_sync(grp, gidx[j]) == gidx[j];
+    }
   }
-  const unsigned mi = __ballot_sync(FULL_MASK, inst);
-  if (mi == 0u) return;
-  const uint32_t ni = (uint32_t)__popc(mi);
-  if (wb.n + ni > WBUF) warp_flush(c, wb);
-  if (inst) {
-    wb.buf[wb.n + __popc(mi & ((1u << lane) - 1u))] = h;
-    const unsigned gm = __match_any_sync(mi, node);
-    if ((int)lane == __ffs(gm) - 1) atomicAdd(&c.cnt[node], (uint32_t)__popc(gm));
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    h[j] = (uint32_t)fmix64(key[j]) & c.hash_mask;
+    k0[j] = lead[j] ? vload(&c.hash[h[j]].key) : 0ull;
   }
-  wb.n += ni;
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    cas[j] = lead[j] && k0[j] == HASH_EMPTY;
+    if (cas[j]) k0[j] = atomicCAS(&c.hash[h[j]].key, HASH_EMPTY, key[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    inst[j] = false;
+    const unsigned long long val = ((unsigned long long)gidx[j] << 32) | rgba[j];
+    if (lead[j]) {
+      if (cas[j] && k0[j] == HASH_EMPTY) {
+        inst[j] = true;
+        atomicMin(&c.hash[h[j]].val, val);
+      } else if (k0[j] == key[j]) {
+        hash_lower(c.hash + h[j], val);
+      } else {
+        inst[j] = hash_claim_rest(c, key[j], val, h[j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const unsigned mi = __ballot_sync(FULL_MASK, inst[j]);
+    if (mi == 0u) continue;
+    const uint32_t ni = (uint32_t)__popc(mi);
+    if (wb.n + ni > WBUF) warp_flush(c, wb);
+    if (inst[j]) {
+      wb.buf[wb.n + __popc(mi & ((1u << lane) - 1u))] = h[j];
+      const unsigned gm = __match_any_sync(mi, node[j]);
+      if ((int)lane == __ffs(gm) - 1) atomicAdd(&c.cnt[node[j]], (uint32_t)__popc(gm));
+    }
+    wb.n += ni;
+  }
 }
 
 // All 32 lanes call. Lanes with `valid` count one point into `leaf` (a
@@ -479,12 +519,20 @@ __device__ void phase_count1(const Ctx& c, uint32_t* smem, uint32_t n_nodes, con
           }
         }
       }
+      bool want[DESCENT_GROUP];
+      unsigned long long key[DESCENT_GROUP];
 #pragma unroll
       for (int k = 0; k < DESCENT_GROUP; ++k) {
-        const bool want = ginner[k] && ((gword[k] >> (gcell[k] & 31u)) & 1u) == 0u;
-        warp_claim(c, wb, want, ((unsigned long long)gnode[k] << (3u * c.G)) | gcell[k], gidx,
-                   (uint32_t)p.w, gnode[k]);
+        want[k] = ginner[k] && ((gword[k] >> (gcell[k] & 31u)) & 1u) == 0u;
+        key[k] = ((unsigned long long)gnode[k] << (3u * c.G)) | gcell[k];
       }
+      uint32_t gg[DESCENT_GROUP], gc[DESCENT_GROUP];
+#pragma unroll
+      for (int k = 0; k < DESCENT_GROUP; ++k) {
+        gg[k] = gidx;
+        gc[k] = (uint32_t)p.w;
+      }
+      warp_claim<DESCENT_GROUP>(c, wb, want, key, gg, gc, gnode);
     }
     warp_tally(c, valid, node);
     if (valid) c.b_cur[i] = node;
@@ -494,90 +542,130 @@ __device__ void phase_count1(const Ctx& c, uint32_t* smem, uint32_t n_nodes, con
 
 // ----------------------------------------------------------- phase: advance
 
-// One item whose cursor node may have split in the previous round: if so it
-// samples that node's grid (empty until store, so every point contends) and
-// moves one level down, counting into the child. Returns true when it moved;
-// cur then holds the new cursor.
-__device__ __forceinline__ bool advance_item(const Ctx& c, NodeCache nc, WarpBuf& wb, bool valid,
-                                             int4 p, uint32_t gidx, uint32_t& cur) {
-  const uint32_t node = cur;
-  const bool in_range = node < c.max_nodes;
-  if (valid && !in_range) set_error(c, E_INTERNAL);
-  const uint32_t ch = (valid && in_range) ? node_child(c, nc, node) : NONE;
-  const bool moving = valid && ch != NONE && ch + 8u <= c.max_nodes;
-  uint32_t rx = 0, ry = 0, rz = 0, L = 0, cell = 0, nxt = 0;
-  if (moving) {
-    rel_coords(c, p, rx, ry, rz);
-    L = c.rlog2 - c.meta[node].level;
-    cell = cell_index(rx, ry, rz, L, c.G);
-    nxt = ch + octant(rx, ry, rz, L);
+constexpr int ADV_U = SL_ADVANCE_UNROLL;
+
+// U items per lane whose cursor node split in the previous round (moving[j]:
+// the cursor cur[j] has children) sample that node's grid (empty until store,
+// so every point contends) and move one level down, counting into the child.
+// cur[j] then holds the new cursor.
+template <int U>
+__device__ __forceinline__ void advance_items(const Ctx& c, WarpBuf& wb, const bool (&moving)[U],
+                                              const int4 (&p)[U], const uint32_t (&gidx)[U],
+                                              const uint32_t (&ch)[U], uint32_t (&cur)[U]) {
+  uint32_t lvl[U], nxt[U], rgba[U];
+  unsigned long long key[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) lvl[j] = moving[j] ? c.meta[cur[j]].level : 0u;
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    uint32_t rx = 0, ry = 0, rz = 0, cell = 0;
+    nxt[j] = cur[j];
+    if (moving[j]) {
+      rel_coords(c, p[j], rx, ry, rz);
+      const uint32_t L = c.rlog2 - lvl[j];
+      cell = cell_index(rx, ry, rz, L, c.G);
+      nxt[j] = ch[j] + octant(rx, ry, rz, L);
+    }
+    key[j] = ((unsigned long long)cur[j] << (3u * c.G)) | cell;
+    rgba[j] = (uint32_t)p[j].w;
   }
-  warp_claim(c, wb, moving, ((unsigned long long)node << (3u * c.G)) | cell, gidx, (uint32_t)p.w,
-             node);
-  warp_tally(c, moving, nxt);
-  if (moving) cur = nxt;
-  return moving;
+  warp_claim<U>(c, wb, moving, key, gidx, rgba, cur);
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    warp_tally(c, moving[j], nxt[j]);
+    cur[j] = nxt[j];
+  }
 }
 
-// Round of the expansion after the first: the batch points, then the spill
-// tasks [0, t_hi) (tasks [t_lo, t_hi) are new: their points still sit at the
-// split leaf), and zeroing the grids of the splits [s_lo, s_hi) of the
-// previous round. Work is cut into warp units so that all warps share it.
+// Round of the expansion after the first: zero the grids of the splits
+// [s_lo, s_hi) of the previous round, then move the batch points and the
+// points of the spill tasks [0, t_hi) (tasks [t_lo, t_hi) are new: their
+// points still sit at the split leaf) whose cursor node split. Points are
+// cut into 32-item warp units (a unit of a task never crosses into the next
+// task); each warp takes U units at a time so that their L2 round trips
+// overlap.
 __device__ void phase_advance(const Ctx& c, uint32_t* smem, uint32_t n_nodes, const int4* pts,
                               uint64_t n, unsigned long long base, uint32_t t_lo, uint32_t t_hi,
                               uint32_t s_lo, uint32_t s_hi, uint64_t warp0, uint64_t nwarps) {
+  constexpr int U = ADV_U;
   const NodeCache nc = load_node_cache(c, smem, n_nodes);
   WarpBuf wb = warp_buf(smem);
   const uint32_t lane = lane_id();
   const uint32_t zpg = (c.grid_bytes + ZERO_UNIT - 1) / ZERO_UNIT;  // zero units per grid
-  const uint32_t parts = (c.C + TASK_PART - 1) / TASK_PART;       // units per task
   const uint64_t uz = (uint64_t)(s_hi - s_lo) * zpg;
+  for (uint64_t w = warp0; w < uz; w += nwarps) {
+    const uint32_t id = c.splits[s_lo + (uint32_t)(w / zpg)].node;
+    const uint32_t gref = id < c.max_nodes ? c.gridref[id] : NONE;
+    if (!ref_ok(c, gref, c.grid_bytes)) {
+      if (lane == 0) set_error(c, E_INTERNAL);
+      continue;
+    }
+    const uint32_t lo = (uint32_t)(w % zpg) * ZERO_UNIT;
+    const uint32_t hi = min(lo + ZERO_UNIT, c.grid_bytes);
+    int4* g = reinterpret_cast<int4*>(grid_words(c, gref));
+    for (uint32_t b = lo / 16 + lane; b < hi / 16; b += 32) g[b] = make_int4(0, 0, 0, 0);
+  }
+  const uint32_t parts = (c.C + 31) / 32;  // units per task
   const uint64_t ub = (n + 31) / 32;
-  const uint64_t ut = (uint64_t)t_hi * parts;
-  for (uint64_t w = warp0; w < uz + ub + ut; w += nwarps) {
-    if (w < uz) {
-      const uint32_t id = c.splits[s_lo + (uint32_t)(w / zpg)].node;
-      const uint32_t gref = id < c.max_nodes ? c.gridref[id] : NONE;
-      if (!ref_ok(c, gref, c.grid_bytes)) {
-        if (lane == 0) set_error(c, E_INTERNAL);
-        continue;
+  const uint64_t units = ub + (uint64_t)t_hi * parts;
+  for (uint64_t w0 = warp0; w0 < units; w0 += U * nwarps) {
+    bool valid[U], moving[U], spill[U];
+    uint32_t cur[U], ch[U], gidx[U], src[U], e[U];
+    int4 p[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const uint64_t w = w0 + j * nwarps;
+      spill[j] = w >= ub;
+      valid[j] = false;
+      cur[j] = 0;
+      src[j] = NONE;
+      e[j] = 0;
+      gidx[j] = 0;
+      if (w < ub) {
+        const uint64_t i = w * 32 + lane;
+        valid[j] = i < n;
+        cur[j] = valid[j] ? c.b_cur[i] : 0u;
+        gidx[j] = (uint32_t)(base + i);
+        e[j] = (uint32_t)i;
+      } else if (w < units) {
+        const uint64_t u = w - ub;
+        const uint32_t t = (uint32_t)(u / parts), q = (uint32_t)(u % parts) * 32u + lane;
+        const SpillTask tk = c.tasks[t];
+        const bool task_ok = ref_ok(c, tk.ref, c.chunk_bytes) && tk.n <= c.C &&
+                             (unsigned long long)tk.dst + tk.n <= c.spill_cap;
+        if (!task_ok && lane == 0) set_error(c, E_INTERNAL);
+        valid[j] = task_ok && q < tk.n;
+        e[j] = tk.dst + q;
+        src[j] = tk.ref;
+        gidx[j] = q;  // index in the chunk until the point is read
+        cur[j] = valid[j] ? (t >= t_lo ? tk.node : c.sp_cur[e[j]]) : 0u;
       }
-      const uint32_t lo = (uint32_t)(w % zpg) * ZERO_UNIT;
-      const uint32_t hi = min(lo + ZERO_UNIT, c.grid_bytes);
-      int4* g = reinterpret_cast<int4*>(grid_words(c, gref));
-      for (uint32_t b = lo / 16 + lane; b < hi / 16; b += 32) g[b] = make_int4(0, 0, 0, 0);
-    } else if (w < uz + ub) {
-      const uint64_t i = (w - uz) * 32 + lane;
-      const bool valid = i < n;
-      uint32_t cur = valid ? c.b_cur[i] : 0u;
-      // read the point only when its cursor node split (it moves)
-      const bool may_move = valid && cur < c.max_nodes && node_child(c, nc, cur) != NONE;
-      const int4 p = may_move ? __ldg(pts + i) : make_int4(0, 0, 0, 0);
-      if (advance_item(c, nc, wb, valid, p, (uint32_t)(base + i), cur)) c.b_cur[i] = cur;
-    } else {
-      const uint64_t u = w - uz - ub;
-      const uint32_t t = (uint32_t)(u / parts), part = (uint32_t)(u % parts);
-      const SpillTask tk = c.tasks[t];
-      const bool task_ok = ref_ok(c, tk.ref, c.chunk_bytes) && tk.n <= c.C &&
-                           (unsigned long long)tk.dst + tk.n <= c.spill_cap;
-      if (!task_ok) {
-        if (lane == 0) set_error(c, E_INTERNAL);
-        continue;
+    }
+    // read a point only when its cursor node split (it moves)
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      if (valid[j] && cur[j] >= c.max_nodes) {
+        set_error(c, E_INTERNAL);
+        valid[j] = false;
       }
-      const bool fresh = t >= t_lo;
-      const uint32_t q_end = min(tk.n, (part + 1) * TASK_PART);
-      for (uint32_t q0 = part * TASK_PART; q0 < q_end; q0 += 32) {
-        const uint32_t q = q0 + lane;
-        const bool valid = q < q_end;
-        const uint32_t e = tk.dst + q;
-        uint32_t cur = valid ? (fresh ? tk.node : c.sp_cur[e]) : 0u;
-        // read the point only when its cursor node split (it moves)
-        const uint32_t ch = (valid && cur < c.max_nodes) ? node_child(c, nc, cur) : NONE;
-        const bool may_move = ch != NONE;
-        const int4 p = may_move ? chunk_recs(c, tk.ref)[q] : make_int4(0, 0, 0, 0);
-        const uint32_t g = may_move ? chunk_aux(c, tk.ref)[q] : 0u;
-        if (advance_item(c, nc, wb, valid, p, g, cur)) c.sp_cur[e] = cur;
+      ch[j] = valid[j] ? node_child(c, nc, cur[j]) : NONE;
+      moving[j] = ch[j] != NONE && ch[j] + 8u <= c.max_nodes;
+      p[j] = make_int4(0, 0, 0, 0);
+      if (moving[j]) {
+        if (spill[j]) {
+          p[j] = chunk_recs(c, src[j])[gidx[j]];
+          gidx[j] = chunk_aux(c, src[j])[gidx[j]];
+        } else {
+          p[j] = __ldg(pts + e[j]);
+        }
       }
+    }
+    advance_items<U>(c, wb, moving, p, gidx, ch, cur);
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      if (!moving[j]) continue;
+      if (spill[j]) c.sp_cur[e[j]] = cur[j];
+      else c.b_cur[e[j]] = cur[j];
     }
   }
   warp_flush(c, wb);
@@ -596,73 +684,114 @@ __device__ __forceinline__ uint32_t pool_take(const Ctx& c, uint32_t k, int* fir
   return (uint32_t)take;
 }
 
-// Section 5.3: give node `id` ceil(total / C) chunks, pool first, then the
-// bump allocator; link them, note them in a leaf's directory and record the
-// store map for this update.
+// Section 5.3, all 32 lanes of a warp call with the same arguments: give
+// node `id` ceil(total / C) chunks, pool first, then the bump allocator; link
+// them, note them in a leaf's directory and record the store map for this
+// update. Lane 0 takes the allocator atomics; the lanes link the new chunks
+// in parallel (chunk q's successor is chunk q + 1 of the same allocation).
 __device__ void alloc_chunks(const Ctx& c, uint32_t id, uint32_t total, bool leaf) {
+  const uint32_t lane = lane_id();
   NodeMeta& m = c.meta[id];
-  const uint32_t have = m.n_chunks;
+  const uint32_t have = m.n_chunks, tail = m.tail, mdir = m.dir;
   const uint32_t need = (uint32_t)(((unsigned long long)total + c.C - 1) / c.C);
-  m.st_nch = have;
-  m.st_tail = m.tail;
-  m.st_seq = 0;
-  m.st_base = c.num[id];
-  c.scur[id] = 0;
-  if (need <= have) return;
-  const uint32_t k = need - have;
-  const uint32_t seq = atomicAdd(&c.ctl->alloc_seq, k);
-  if ((unsigned long long)seq + k > c.max_chunks) {
-    set_error(c, E_ALLOC_REFS);
-    return;
-  }
-  m.st_seq = seq;
+  const uint32_t k = need > have ? need - have : 0u;
+  uint32_t seq = 0, from_pool = 0, ok = 1;
   int pfirst = 0;
-  const uint32_t from_pool = pool_take(c, k, &pfirst);
-  const uint32_t rest = k - from_pool;
   unsigned long long off = 0;
-  if (rest) {
-    off = atomicAdd(&c.ctl->bump, (unsigned long long)rest * c.chunk_bytes);
-    if (off + (unsigned long long)rest * c.chunk_bytes > c.data_bytes) {
-      set_error(c, E_ARENA);
-      return;
+  if (lane == 0 && k) {
+    seq = atomicAdd(&c.ctl->alloc_seq, k);
+    if ((unsigned long long)seq + k > c.max_chunks) {
+      set_error(c, E_ALLOC_REFS);
+      ok = 0;
+    } else {
+      from_pool = pool_take(c, k, &pfirst);
+      const uint32_t rest = k - from_pool;
+      if (rest) {
+        off = atomicAdd(&c.ctl->bump, (unsigned long long)rest * c.chunk_bytes);
+        if (off + (unsigned long long)rest * c.chunk_bytes > c.data_bytes) {
+          set_error(c, E_ARENA);
+          ok = 0;
+        } else {
+          atomicAdd(&c.ctl->chunks_bumped, (unsigned long long)rest);
+        }
+      }
     }
-    atomicAdd(&c.ctl->chunks_bumped, (unsigned long long)rest);
   }
-  uint32_t* dir = (leaf && ref_ok(c, m.dir, c.dir_bytes)) ? dir_entries(c, m.dir) : nullptr;
-  uint32_t prev = m.tail;
-  for (uint32_t q = 0; q < k; ++q) {
-    uint32_t ref = q < from_pool ? c.pool[pfirst + (int)q]
-                                 : (uint32_t)(off / REF_BYTES) + (q - from_pool) * c.chunk_units;
+  seq = __shfl_sync(FULL_MASK, seq, 0);
+  from_pool = __shfl_sync(FULL_MASK, from_pool, 0);
+  pfirst = __shfl_sync(FULL_MASK, pfirst, 0);
+  off = __shfl_sync(FULL_MASK, off, 0);
+  ok = __shfl_sync(FULL_MASK, ok, 0);
+  if (lane == 0) {
+    m.st_nch = have;
+    m.st_tail = tail;
+    m.st_seq = k ? seq : 0u;
+    m.st_base = c.num[id];
+    c.scur[id] = 0;
+  }
+  if (!k || !ok) return;
+  uint32_t* dir = (leaf && ref_ok(c, mdir, c.dir_bytes)) ? dir_entries(c, mdir) : nullptr;
+  const uint32_t bump_ref = (uint32_t)(off / REF_BYTES);
+  auto ref_of = [&](uint32_t q) -> uint32_t {
+    return q < from_pool ? c.pool[pfirst + (int)q] : bump_ref + (q - from_pool) * c.chunk_units;
+  };
+  for (uint32_t q = lane; q < k; q += 32) {
+    const uint32_t ref = ref_of(q);
+    const uint32_t nxt = q + 1u < k ? ref_of(q + 1u) : NONE;
     c.alloc_refs[seq + q] = ref;
-    *chunk_next(c, ref) = NONE;
-    if (prev == NONE) m.head = ref;
-    else *chunk_next(c, prev) = ref;
+    *chunk_next(c, ref) = nxt;
     if (dir && have + q < c.dir_cap) dir[have + q] = ref;
-    prev = ref;
+    if (q == 0) {
+      if (tail == NONE) m.head = ref;
+      else *chunk_next(c, tail) = ref;
+    }
+    if (q + 1u == k) m.tail = ref;
   }
-  m.tail = prev;
-  m.n_chunks = need;
+  if (lane == 0) m.n_chunks = need;
 }
 
-// Section 5.1: split leaf `id` whose count exceeds T: 8 children (with chunk
-// directories), a grid for the node (zeroed in the next round), and one spill
-// task per chunk of its stored points; those chunks return to the pool at the
-// end of the update.
+// Section 5.1, all 32 lanes of a warp call: split leaf `id` whose count
+// exceeds T: 8 children (with chunk directories), a grid for the node (zeroed
+// in the next round), and one spill task per chunk of its stored points;
+// those chunks return to the pool at the end of the update.
 __device__ void split_leaf(const Ctx& c, uint32_t id) {
-  const uint32_t c0 = atomicAdd(&c.ctl->n_nodes, 8u);
-  if ((unsigned long long)c0 + 8 > c.max_nodes) {
-    set_error(c, E_NODES);
-    return;
-  }
-  const unsigned long long dbase = atomicAdd(&c.ctl->bump, 8ull * c.dir_bytes);
-  const unsigned long long g = atomicAdd(&c.ctl->bump, (unsigned long long)c.grid_bytes);
-  if (dbase + 8ull * c.dir_bytes > c.data_bytes || g + c.grid_bytes > c.data_bytes) {
-    set_error(c, E_ARENA);
-    return;
-  }
+  const uint32_t lane = lane_id();
   NodeMeta& m = c.meta[id];
-  const uint32_t Lc = c.rlog2 - m.level - 1u;  // children's log2 size
-  for (uint32_t k = 0; k < 8; ++k) {
+  const uint32_t stored = c.num[id], nch = m.n_chunks, mdir = m.dir;
+  uint32_t c0 = 0, s0 = 0, t0 = 0, e = 0, ok = 1;
+  unsigned long long dbase = 0, g = 0;
+  if (lane == 0) {
+    c0 = atomicAdd(&c.ctl->n_nodes, 8u);
+    dbase = atomicAdd(&c.ctl->bump, 8ull * c.dir_bytes + c.grid_bytes);
+    g = dbase + 8ull * c.dir_bytes;
+    s0 = atomicAdd(&c.ctl->spill_count, stored);
+    t0 = atomicAdd(&c.ctl->ntasks, nch);
+    e = atomicAdd(&c.ctl->split_count, 1u);
+    if ((unsigned long long)c0 + 8 > c.max_nodes || e >= c.max_splits) {
+      set_error(c, E_NODES);
+      ok = 0;
+    } else if (g + c.grid_bytes > c.data_bytes) {
+      set_error(c, E_ARENA);
+      ok = 0;
+    } else if ((unsigned long long)s0 + stored > c.spill_cap) {
+      set_error(c, E_SPILL);
+      ok = 0;
+    } else if ((unsigned long long)t0 + nch > c.max_chunks || nch > c.dir_cap ||
+               (nch && !ref_ok(c, mdir, c.dir_bytes))) {
+      set_error(c, E_INTERNAL);
+      ok = 0;
+    }
+  }
+  if (!__shfl_sync(FULL_MASK, ok, 0)) return;
+  c0 = __shfl_sync(FULL_MASK, c0, 0);
+  s0 = __shfl_sync(FULL_MASK, s0, 0);
+  t0 = __shfl_sync(FULL_MASK, t0, 0);
+  e = __shfl_sync(FULL_MASK, e, 0);
+  dbase = __shfl_sync(FULL_MASK, dbase, 0);
+  g = __shfl_sync(FULL_MASK, g, 0);
+  if (lane < 8) {
+    const uint32_t k = lane;
+    const uint32_t Lc = c.rlog2 - m.level - 1u;  // children's log2 size
     NodeMeta cm;
     cm.min[0] = m.min[0] + (int32_t)((k & 1u) << Lc);
     cm.min[1] = m.min[1] + (int32_t)(((k >> 1) & 1u) << Lc);
@@ -682,67 +811,56 @@ __device__ void split_leaf(const Ctx& c, uint32_t id) {
     c.cnt[c0 + k] = 0;
     c.num[c0 + k] = 0;
   }
-  const uint32_t stored = c.num[id];
-  const uint32_t nch = m.n_chunks;
-  const uint32_t s0 = atomicAdd(&c.ctl->spill_count, stored);
-  const uint32_t t0 = atomicAdd(&c.ctl->ntasks, nch);
-  if ((unsigned long long)s0 + stored > c.spill_cap) {
-    set_error(c, E_SPILL);
-    return;
-  }
-  if ((unsigned long long)t0 + nch > c.max_chunks || nch > c.dir_cap ||
-      (nch && !ref_ok(c, m.dir, c.dir_bytes))) {
-    set_error(c, E_INTERNAL);
-    return;
-  }
-  const uint32_t* dir = nch ? dir_entries(c, m.dir) : nullptr;
-  for (uint32_t j = 0; j < nch; ++j) {
+  const uint32_t* dir = nch ? dir_entries(c, mdir) : nullptr;
+  for (uint32_t j = lane; j < nch; j += 32) {
     const uint32_t ref = dir[j];
     const uint32_t first = j * c.C;
     c.tasks[t0 + j] = SpillTask{ref, id, s0 + first, min(c.C, stored - first)};
     c.pending[t0 + j] = ref;
   }
-  const uint32_t e = atomicAdd(&c.ctl->split_count, 1u);
-  if (e >= c.max_splits) {
-    set_error(c, E_NODES);
-    return;
+  __syncwarp();  // every lane has read m before lane 0 rewrites it
+  if (lane == 0) {
+    c.splits[e] = SplitEntry{id, s0};
+    c.gridref[id] = (uint32_t)(g / REF_BYTES);
+    m.n_chunks = 0;
+    m.head = m.tail = NONE;
+    m.dir = NONE;
+    c.num[id] = 0;
+    c.cnt[id] = 0;
+    c.child[id] = c0;
   }
-  c.splits[e] = SplitEntry{id, s0};
-  c.gridref[id] = (uint32_t)(g / REF_BYTES);
-  m.n_chunks = 0;
-  m.head = m.tail = NONE;
-  m.dir = NONE;
-  c.num[id] = 0;
-  c.cnt[id] = 0;
-  c.child[id] = c0;
 }
 
+// All 32 lanes of a warp call for one candidate node.
 __device__ __forceinline__ void decide_node(const Ctx& c, uint32_t id) {
   const uint32_t k = c.cnt[id];
   if (k == 0) return;
+  const uint32_t num = c.num[id];
   if (c.child[id] == NONE) {
-    const uint32_t total = c.num[id] + k;
+    const uint32_t total = num + k;
     const uint32_t L = c.rlog2 - c.meta[id].level;
     if (total > c.T && L > 0) {
       split_leaf(c, id);
       return;
     }
     alloc_chunks(c, id, total, true);
-    c.num[id] = total;
+    __syncwarp();
+    if (lane_id() == 0) c.num[id] = total;
   } else {
-    alloc_chunks(c, id, c.num[id] + k, false);
-    c.num[id] += k;
+    alloc_chunks(c, id, num + k, false);
+    __syncwarp();
+    if (lane_id() == 0) c.num[id] = num + k;
   }
-  c.cnt[id] = 0;
+  if (lane_id() == 0) c.cnt[id] = 0;
 }
 
-// Candidates: the nodes split in the previous round (their voxels are now
-// all claimed) and the node id range [n_lo, n_hi).
+// Candidates, one warp each: the nodes split in the previous round (their
+// voxels are now all claimed) and the node id range [n_lo, n_hi).
 __device__ void phase_decide(const Ctx& c, uint32_t s_lo, uint32_t s_hi, uint32_t n_lo,
-                             uint32_t n_hi, uint64_t t0, uint64_t nthreads) {
+                             uint32_t n_hi, uint64_t warp0, uint64_t nwarps) {
   const uint64_t ns = s_hi - s_lo, nn = n_hi - n_lo;
-  for (uint64_t t = t0; t < ns + nn; t += nthreads) {
-    uint32_t id = t < ns ? c.splits[s_lo + t].node : (uint32_t)(n_lo + (t - ns));
+  for (uint64_t w = warp0; w < ns + nn; w += nwarps) {
+    const uint32_t id = w < ns ? c.splits[s_lo + w].node : (uint32_t)(n_lo + (w - ns));
     decide_node(c, id);
   }
 }
@@ -761,92 +879,184 @@ __device__ void phase_rollback(const Ctx& c, uint32_t n_nodes, uint64_t t0, uint
 
 // -------------------------------------------------------------- phase: store
 
-__device__ __forceinline__ void store_rec(const Ctx& c, uint32_t node, uint32_t slot, int4 rec,
-                                          uint32_t aux) {
-  if (node >= c.max_nodes) {
-    set_error(c, E_INTERNAL);
-    return;
+// All 32 lanes call with U items each (warp-uniform). Every valid item gets
+// the next free slot of its node in this update: the node's records before
+// the update (st_base) + a running per-node cursor, one atomicAdd per
+// distinct node per warp and item index; the store map then turns the slot
+// into (chunk ref, index in chunk). The map (st_nch, st_tail, st_seq,
+// st_base) is one 16-byte load per item, issued with the cursor atomics.
+// Invalid items, and items whose slot has no chunk, get ref NONE (the latter
+// raise E_INTERNAL).
+template <int U>
+__device__ __forceinline__ void warp_place(const Ctx& c, const bool (&valid)[U],
+                                           const uint32_t (&node)[U], uint32_t (&ref)[U],
+                                           uint32_t (&q)[U]) {
+  const uint32_t lane = lane_id();
+  uint4 map[U];
+  uint32_t rank[U], cur[U];
+  int leader[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    map[j] = valid[j] ? *reinterpret_cast<const uint4*>(&c.meta[node[j]].st_nch)
+                      : make_uint4(0, NONE, 0, 0);
   }
-  const NodeMeta& m = c.meta[node];
-  const uint32_t j = slot / c.C, q = slot - j * c.C;
-  uint32_t ref = NONE;
-  if (j + 1u == m.st_nch) {
-    ref = m.st_tail;
-  } else if (j >= m.st_nch) {
-    const unsigned long long at = (unsigned long long)m.st_seq + (j - m.st_nch);
-    if (at < c.max_chunks) ref = c.alloc_refs[at];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const unsigned m = __ballot_sync(FULL_MASK, valid[j]);
+    leader[j] = 0;
+    rank[j] = 0;
+    cur[j] = 0;
+    if (valid[j]) {
+      const unsigned grp = __match_any_sync(m, node[j]);
+      leader[j] = __ffs(grp) - 1;
+      rank[j] = __popc(grp & ((1u << lane) - 1u));
+      if ((int)lane == leader[j]) cur[j] = atomicAdd(&c.scur[node[j]], (uint32_t)__popc(grp));
+    }
   }
-  if (!ref_ok(c, ref, c.chunk_bytes)) {
-    set_error(c, E_INTERNAL);
-    return;
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    cur[j] = __shfl_sync(FULL_MASK, cur[j], leader[j]);
+    ref[j] = NONE;
+    q[j] = 0;
+    if (valid[j]) {
+      const uint32_t slot = map[j].w + cur[j] + rank[j];
+      const uint32_t k = slot / c.C;
+      q[j] = slot - k * c.C;
+      if (k + 1u == map[j].x) {
+        ref[j] = map[j].y;
+      } else if (k >= map[j].x) {
+        const unsigned long long at = (unsigned long long)map[j].z + (k - map[j].x);
+        if (at < c.max_chunks) ref[j] = c.alloc_refs[at];
+      }
+    }
   }
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    if (valid[j] && !ref_ok(c, ref[j], c.chunk_bytes)) {
+      set_error(c, E_INTERNAL);
+      ref[j] = NONE;
+    }
+  }
+}
+
+__device__ __forceinline__ void put_rec(const Ctx& c, uint32_t ref, uint32_t q, int4 rec,
+                                        uint32_t aux) {
+  if (ref == NONE) return;
   chunk_recs(c, ref)[q] = rec;
   chunk_aux(c, ref)[q] = aux;
 }
+
+constexpr int STORE_U = SL_STORE_UNROLL;
 
 // Store the batch points, the re-inserted points of the spill tasks [0,
 // n_tasks) and the n_keys new voxels, each at the next free slot of its node;
 // hand the chunks of split leaves (one per task) to the pool above pool_top
 // (the caller then raises pool_top). Loops are warp-uniform so that the
-// lanes of a warp share one slot reservation per node.
+// lanes of a warp share one slot reservation per node; each lane carries
+// STORE_U items at a time so that their L2 round trips overlap.
 __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned long long base,
                             uint32_t n_tasks, uint32_t n_keys, int pool_top, uint64_t t0,
                             uint64_t nthreads) {
+  constexpr int U = STORE_U;
   const uint32_t lane = lane_id();
   const uint64_t w0 = t0 - lane, wstride = nthreads;  // warp-aligned start and stride
-  for (uint64_t b0 = w0; b0 < n; b0 += wstride) {
-    const uint64_t i = b0 + lane;
-    const bool valid = i < n;
-    const uint32_t node = valid ? c.b_cur[i] : 0u;
-    const bool ok = valid && node < c.max_nodes;
-    if (valid && !ok) set_error(c, E_INTERNAL);
-    const uint32_t slot = warp_slot(c, ok, node);
-    if (ok) store_rec(c, node, slot, __ldg(pts + i), (uint32_t)(base + i));
+  for (uint64_t b0 = w0; b0 < n; b0 += U * wstride) {
+    bool valid[U];
+    uint32_t node[U], ref[U], q[U];
+    int4 p[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const uint64_t i = b0 + j * wstride + lane;
+      valid[j] = i < n;
+      node[j] = valid[j] ? c.b_cur[i] : 0u;
+      p[j] = valid[j] ? __ldg(pts + i) : make_int4(0, 0, 0, 0);
+      if (valid[j] && node[j] >= c.max_nodes) {
+        set_error(c, E_INTERNAL);
+        valid[j] = false;
+      }
+    }
+    warp_place<U>(c, valid, node, ref, q);
+#pragma unroll
+    for (int j = 0; j < U; ++j) put_rec(c, ref[j], q[j], p[j], (uint32_t)(base + b0 + j * wstride + lane));
   }
   const uint64_t tp = (uint64_t)n_tasks * c.C;
-  for (uint64_t b0 = w0; b0 < tp; b0 += wstride) {
-    const uint64_t u = b0 + lane;
-    bool valid = u < tp;
-    const uint32_t t = valid ? (uint32_t)(u / c.C) : 0u;
-    const uint32_t q = valid ? (uint32_t)(u - (uint64_t)t * c.C) : 0u;
-    SpillTask tk = valid ? c.tasks[t] : SpillTask{NONE, 0, 0, 0};
-    valid = valid && q < tk.n;
-    if (valid && (!ref_ok(c, tk.ref, c.chunk_bytes) ||
-                  (unsigned long long)tk.dst + tk.n > c.spill_cap)) {
-      set_error(c, E_INTERNAL);
-      valid = false;
+  for (uint64_t b0 = w0; b0 < tp; b0 += U * wstride) {
+    bool valid[U];
+    uint32_t node[U], ref[U], q[U], src[U], qs[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const uint64_t u = b0 + j * wstride + lane;
+      valid[j] = u < tp;
+      const uint32_t t = valid[j] ? (uint32_t)(u / c.C) : 0u;
+      qs[j] = valid[j] ? (uint32_t)(u - (uint64_t)t * c.C) : 0u;
+      const SpillTask tk = valid[j] ? c.tasks[t] : SpillTask{NONE, 0, 0, 0};
+      valid[j] = valid[j] && qs[j] < tk.n;
+      if (valid[j] && (!ref_ok(c, tk.ref, c.chunk_bytes) ||
+                       (unsigned long long)tk.dst + tk.n > c.spill_cap)) {
+        set_error(c, E_INTERNAL);
+        valid[j] = false;
+      }
+      src[j] = tk.ref;
+      node[j] = valid[j] ? c.sp_cur[tk.dst + qs[j]] : 0u;
+      if (valid[j] && node[j] >= c.max_nodes) {
+        set_error(c, E_INTERNAL);
+        valid[j] = false;
+      }
     }
-    const uint32_t node = valid ? c.sp_cur[tk.dst + q] : 0u;
-    const bool ok = valid && node < c.max_nodes;
-    if (valid && !ok) set_error(c, E_INTERNAL);
-    const uint32_t slot = warp_slot(c, ok, node);
-    if (ok) store_rec(c, node, slot, chunk_recs(c, tk.ref)[q], chunk_aux(c, tk.ref)[q]);
+    int4 r[U];
+    uint32_t g[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      r[j] = valid[j] ? chunk_recs(c, src[j])[qs[j]] : make_int4(0, 0, 0, 0);
+      g[j] = valid[j] ? chunk_aux(c, src[j])[qs[j]] : 0u;
+    }
+    warp_place<U>(c, valid, node, ref, q);
+#pragma unroll
+    for (int j = 0; j < U; ++j) put_rec(c, ref[j], q[j], r[j], g[j]);
   }
   const uint32_t G = c.G, cmask = (1u << (3u * G)) - 1u, amask = (1u << G) - 1u;
-  for (uint64_t b0 = w0; b0 < n_keys; b0 += wstride) {
-    const uint64_t e = b0 + lane;
-    const bool valid = e < n_keys;
-    HSlot* s = valid ? c.hash + c.keys[e] : nullptr;
-    const unsigned long long key = valid ? s->key : 0ull, val = valid ? s->val : 0ull;
-    const uint32_t node = (uint32_t)(key >> (3u * G)), cell = (uint32_t)key & cmask;
-    const uint32_t gref = (valid && node < c.max_nodes) ? c.gridref[node] : NONE;
-    const bool ok = valid && ref_ok(c, gref, c.grid_bytes);
-    if (valid && !ok) set_error(c, E_INTERNAL);
-    const uint32_t slot = warp_slot(c, ok, node);
-    if (!ok) continue;
-    const NodeMeta& m = c.meta[node];
-    const uint32_t L = c.rlog2 - m.level;
-    const uint32_t cx = cell & amask, cy = (cell >> G) & amask, cz = cell >> (2u * G);
-    // Section 3.4: the voxel is a point at the (floor of the) cell centre
-    int4 v;
-    v.x = m.min[0] + (int32_t)(((2ull * cx + 1ull) << L) >> (G + 1u));
-    v.y = m.min[1] + (int32_t)(((2ull * cy + 1ull) << L) >> (G + 1u));
-    v.z = m.min[2] + (int32_t)(((2ull * cz + 1ull) << L) >> (G + 1u));
-    v.w = (int32_t)(uint32_t)val;
-    store_rec(c, node, slot, v, cell);
-    atomicOr(grid_words(c, gref) + (cell >> 5), 1u << (cell & 31u));
-    s->key = HASH_EMPTY;
-    s->val = HASH_EMPTY;
+  for (uint64_t b0 = w0; b0 < n_keys; b0 += U * wstride) {
+    bool valid[U];
+    uint32_t node[U], ref[U], q[U], cell[U], gref[U], rgba[U];
+    HSlot* sl[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const uint64_t e = b0 + j * wstride + lane;
+      valid[j] = e < n_keys;
+      sl[j] = valid[j] ? c.hash + c.keys[e] : nullptr;
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const unsigned long long key = valid[j] ? sl[j]->key : 0ull;
+      rgba[j] = valid[j] ? (uint32_t)sl[j]->val : 0u;
+      node[j] = (uint32_t)(key >> (3u * G));
+      cell[j] = (uint32_t)key & cmask;
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      gref[j] = (valid[j] && node[j] < c.max_nodes) ? c.gridref[node[j]] : NONE;
+      const bool ok = valid[j] && ref_ok(c, gref[j], c.grid_bytes);
+      if (valid[j] && !ok) set_error(c, E_INTERNAL);
+      valid[j] = ok;
+    }
+    warp_place<U>(c, valid, node, ref, q);
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      if (!valid[j]) continue;
+      const NodeMeta& m = c.meta[node[j]];
+      const uint32_t L = c.rlog2 - m.level;
+      const uint32_t cx = cell[j] & amask, cy = (cell[j] >> G) & amask, cz = cell[j] >> (2u * G);
+      // Section 3.4: the voxel is a point at the (floor of the) cell centre
+      int4 v;
+      v.x = m.min[0] + (int32_t)(((2ull * cx + 1ull) << L) >> (G + 1u));
+      v.y = m.min[1] + (int32_t)(((2ull * cy + 1ull) << L) >> (G + 1u));
+      v.z = m.min[2] + (int32_t)(((2ull * cz + 1ull) << L) >> (G + 1u));
+      v.w = (int32_t)rgba[j];
+      put_rec(c, ref[j], q[j], v, cell[j]);
+      atomicOr(grid_words(c, gref[j]) + (cell[j] >> 5), 1u << (cell[j] & 31u));
+      sl[j]->key = HASH_EMPTY;
+      sl[j]->val = HASH_EMPTY;
+    }
   }
   const int top = pool_top > 0 ? pool_top : 0;
   if ((unsigned long long)top + n_tasks > c.max_chunks) {

@@ -43,11 +43,6 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-template <typename T>
-__device__ __forceinline__ T vload(const T* p) {
-  return *reinterpret_cast<const volatile T*>(p);
-}
-
 // Grid-wide barrier with a time limit. Returns false when the launch was
 // aborted (by this block's timeout or another's).
 __device__ __forceinline__ bool grid_barrier(const Ctx& c, FusedCtl* f) {
@@ -143,7 +138,7 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
         // t: its spill tasks (tasks below t_lo are older)
         uint32_t s_lo = 0, s_hi = 0, n_lo = 0, n_hi = nodes0, t_lo = 0, t_hi = 0, iters = 1;
         for (;;) {
-          phase_decide(c, s_lo, s_hi, n_lo, n_hi, tid, nthreads);
+          phase_decide(c, s_lo, s_hi, n_lo, n_hi, warp0, nwarps);
           if (!grid_barrier(c, f)) return;
           clk.tick(c, PH_DECIDE);
           const uint32_t sc = vload(&c.ctl->split_count), nn = vload(&c.ctl->n_nodes);

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(BLOCK) k_decide(Ctx c, uint32_t s_lo, uint32_t
     phase_rollback(c, n_hi, t0, nt);
     return;
   }
-  phase_decide(c, s_lo, s_hi, n_lo, n_hi, t0, nt);
+  phase_decide(c, s_lo, s_hi, n_lo, n_hi, t0 / 32, nt / 32);
 }
 
 __global__ void __launch_bounds__(PBLOCK, PHASE_MIN_BLOCKS) k_advance(Ctx c, const int4* pts, uint64_t n,
@@ -383,7 +383,7 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
   });
   if (rc) return poison(h, rc);
   rc = launch(h, K_DECIDE, s, [&] {
-    k_decide<<<grid_for(h, nodes0, BLOCK), BLOCK, 0, s>>>(c, 0, 0, 0, nodes0);
+    k_decide<<<grid_for(h, 32ull * nodes0, BLOCK), BLOCK, 0, s>>>(c, 0, 0, 0, nodes0);
   });
   if (rc) return poison(h, rc);
   if ((rc = read_ctl(h, s))) return poison(h, rc);
@@ -412,7 +412,7 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
     if (rc) return poison(h, rc);
     const uint64_t cand = (uint64_t)(s_hi - s_lo) + (n_hi - n_lo);
     rc = launch(h, K_DECIDE, s, [&] {
-      k_decide<<<grid_for(h, cand, BLOCK), BLOCK, 0, s>>>(c, s_lo, s_hi, n_lo, n_hi);
+      k_decide<<<grid_for(h, 32 * cand, BLOCK), BLOCK, 0, s>>>(c, s_lo, s_hi, n_lo, n_hi);
     });
     if (rc) return poison(h, rc);
     if ((rc = read_ctl(h, s))) return poison(h, rc);
