@@ -199,6 +199,27 @@ def run_reference(args):
     return 0
 
 
+def make_octree(w, root_log2: int):
+    """The octree the bench times for workload w (its capacities follow the
+    workload's largest batch); the full-size tests build the same one."""
+    import torch
+
+    from paper_2310_03567_gb300 import simlod
+    max_batch = int(max(w.counts))
+    # claim table: 2 slots per backlog entry; up to 2 new voxels per batch
+    # point keeps the table (64 MB for 1M-point batches) mostly L2-resident
+    cfg = simlod.default_config(root_min=w.root_min, root_log2=root_log2,
+                                max_batch_points=max_batch,
+                                spill_capacity=max(8 << 20, 2 * max_batch),
+                                backlog_capacity=max(2 << 20, 2 * max_batch),
+                                max_nodes=1 << 21)
+    data_bytes = max(256 << 20, w.n_points * 80)
+    arena = simlod.make_arena(cfg, data_bytes)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    return simlod.Octree(cfg, arena, stream=stream)
+
+
 def rank_workload(name: str, points, rank: int):
     """The workload a rank builds: every rank has its own octree and stream
     (independent units, no data-path collective); rank r > 0 gets its own
@@ -258,18 +279,9 @@ def run_ours(args):
     ptrs = [dev_pts.data_ptr() + int(o) * 16 for o in w.offsets]
     counts = [int(c) for c in w.counts]
     max_batch = max(counts)
-    # claim table: 2 slots per backlog entry; up to 2 new voxels per batch
-    # point keeps the table (64 MB for 1M-point batches) mostly L2-resident
-    cfg = simlod.default_config(root_min=w.root_min, root_log2=root_log2,
-                                max_batch_points=max_batch,
-                                spill_capacity=max(8 << 20, 2 * max_batch),
-                                backlog_capacity=max(2 << 20, 2 * max_batch),
-                                max_nodes=1 << 21)
-    data_bytes = max(256 << 20, n_points * 80)
-    arena = simlod.make_arena(cfg, data_bytes)
-    stream = torch.cuda.Stream()
-    stream.wait_stream(torch.cuda.current_stream())
-    tree = simlod.Octree(cfg, arena, stream=stream)
+    tree = make_octree(w, root_log2)
+    cfg = tree.cfg
+    stream = tree.stream
 
     def check(rc, what):
         if rc != simlod.OK:
@@ -404,7 +416,8 @@ def run_ours(args):
                      "alg_bytes_per_launch": upd_bytes, "peak_source": peak_src},
         "update_roofline": {"alg_bytes_per_point": upd_bytes / B, "roofline_mpts": roofline_mpts,
                             "frac": value / world / roofline_mpts},
-        "update_counts": {"B": B, "S": S, "V": V, "K": K},
+        "update_counts": {"B": B, "S": S, "V": V, "K": K, "rounds": stats["rounds"],
+                          "nodes": stats["nodes"]},
         "fused_phase_ms_per_step": phases,
         "gpu_launches": 2 * args.steps,
         "e2e": {"value": job_points / e2e_s / 1e6, "unit": UNIT,

@@ -64,8 +64,8 @@ typedef struct {
   uint32_t chunk_points;     /* C: records per chunk (1,000; Section 3.4), 1..65,536 */
   uint32_t grid_log2;        /* G: sampling grid 2^G per axis (7 = 128^3; Section 3.3), 1..7 */
   uint32_t max_expand_iters; /* expansion rounds per update; 0 = root_log2 + 1 (enough) */
-  uint64_t max_batch_points; /* largest n accepted by one insert */
-  uint64_t spill_capacity;   /* points re-inserted from split leaves, per update */
+  uint64_t max_batch_points; /* largest n accepted by one insert, 1..2^31-1 */
+  uint64_t spill_capacity;   /* points re-inserted from split leaves, per update, < 2^31 */
   uint64_t backlog_capacity; /* new voxels per update (10M suggested; Section 5.2) */
   uint64_t max_nodes;        /* node table size */
   uint32_t flags;            /* reserved, 0 */

@@ -6,24 +6,23 @@
 //  count1  every batch point walks from the root to its leaf. At every inner
 //          node on the way it tests the node's occupancy bit (Section 3.3);
 //          an empty cell makes the point a contender for a new voxel. At the
-//          leaf it takes a ticket from the leaf's counter (Section 5.1,
-//          "Counting"); the ticket is its final slot if the leaf does not
-//          split. The leaf and ticket are kept per point (the cursor).
+//          leaf it is counted (Section 5.1, "Counting"); the leaf is kept per
+//          point (its cursor).
 //  decide  per candidate node: a leaf whose stored + counted points exceed T
 //          splits (Section 5.1, "Splitting"): 8 children, a grid, and one
 //          spill task per chunk of its stored points. Any other counted node
 //          is final and gets its chunks now (Section 5.3).
 //  advance points whose cursor node split in the previous round (batch
-//          points, and the stored points of split leaves, read in place from
-//          their old chunks through the spill tasks) sample that node's grid
-//          and move one level down, counting into the child; the grids of
-//          the previous round's splits are zeroed alongside. Repeated with
-//          decide until nothing splits: the paper's iterative deepening, but
-//          each round touches only the points that have to move.
-//  store   every point goes to its cursor leaf at its ticket slot; every new
-//          voxel goes to its node (Section 5.4); occupancy bits are set here,
-//          after all claims of the update; the chunks of split leaves return
-//          to the pool (Section 3.4), now that their points were re-stored.
+//          points, and the stored points of split leaves, copied out of their
+//          old chunks at their first move) sample that node's grid and move
+//          one level down, counting into the child; the grids of the previous
+//          round's splits are zeroed alongside. Repeated with decide until
+//          nothing splits: the paper's iterative deepening, but each round
+//          touches only the points that have to move (mover lists).
+//  store   every point goes to its cursor leaf at the next free slot; every
+//          new voxel goes to its node (Section 5.4); occupancy bits are set
+//          here, after all claims of the update; the chunks of split leaves
+//          return to the pool (Section 3.4).
 //
 // Voxel claims: the paper lets the first point that finds an empty cell win.
 // Here all contenders of an update for a (node, cell) meet in an open-
@@ -34,6 +33,8 @@
 // Descents read the node table (first child, grid reference) from a copy in
 // shared memory of the first NODE_CACHE nodes, taken at the start of each
 // count / advance pass; the node ids of the upper levels are the smallest.
+// Per-node counters are summed per block in shared memory before they reach
+// the global counters (the block tally cache).
 #pragma once
 
 #include <cstddef>
@@ -65,11 +66,8 @@ constexpr uint32_t CHUNK_HEADER = 16;
 #ifndef SL_STORE_UNROLL
 #define SL_STORE_UNROLL 2
 #endif
-#ifndef SL_ADVANCE_UNROLL
-#define SL_ADVANCE_UNROLL 1
-#endif
-#ifndef SL_CLAIM_READ_VAL
-#define SL_CLAIM_READ_VAL 0
+#ifndef SL_BLOCK_TALLY
+#define SL_BLOCK_TALLY 1
 #endif
 constexpr uint32_t NODE_CACHE = SL_NODE_CACHE;         // nodes mirrored in shared memory
 constexpr uint32_t NODE_CACHE_BYTES = NODE_CACHE * 8;  // child + grid reference
@@ -79,7 +77,15 @@ constexpr uint32_t WBUF = 64;                          // new-cell slots staged 
 constexpr int PHASE_BLOCK = SL_PHASE_BLOCK;            // threads of count / advance / fused blocks
 constexpr int PHASE_MIN_BLOCKS = SL_PHASE_MIN_BLOCKS;  // resident blocks per SM they aim for
 // dynamic shared memory of the count / advance / fused blocks
-constexpr uint32_t PHASE_SMEM_BYTES = NODE_CACHE_BYTES + (PHASE_BLOCK / 32) * WBUF * 4;
+constexpr uint32_t MVBUF = 128;                         // mover-list entries staged per warp
+constexpr uint32_t TALLY_LOG2 = 9;                      // block tally cache: 512 nodes
+constexpr uint32_t TALLY_SLOTS = 1u << TALLY_LOG2;
+// dynamic shared memory of the count / advance / fused blocks: node cache,
+// new-cell staging, mover staging, block tally cache
+constexpr uint32_t SMEM_WBUF = 2 * NODE_CACHE;                        // in u32 words
+constexpr uint32_t SMEM_MVBUF = SMEM_WBUF + (PHASE_BLOCK / 32) * WBUF;
+constexpr uint32_t SMEM_TALLY = SMEM_MVBUF + (PHASE_BLOCK / 32) * MVBUF * 4;
+constexpr uint32_t PHASE_SMEM_BYTES = 4 * (SMEM_TALLY + 2 * TALLY_SLOTS);
 
 // Sticky device error bits.
 enum : uint32_t {
@@ -113,7 +119,8 @@ struct Ctl {
       st_iter_max, st_rounds;
   unsigned long long last_points, last_spilled, last_splits, last_voxels, last_iters;
   unsigned long long st_rejected_async;  // rejections inside fused launches
-  unsigned long long pad1[2];
+  unsigned int mv_count[2];              // entries of the two mover lists
+  unsigned long long pad1;
   unsigned long long phase_ns[8];        // fused form: time per phase (see PH_*)
 };
 static_assert(sizeof(Ctl) % 16 == 0, "Ctl size");
@@ -171,8 +178,11 @@ struct Ctx {
   SplitEntry* splits;
   SpillTask* tasks;
   uint32_t* sp_cur;   // per spill entry: cursor node (after its first move)
+  int4* sp_rec;       // per spill entry: the point, copied at its first move
+  uint32_t* sp_gidx;  //   and its gidx
   uint32_t* b_cur;    // per batch point: cursor node
   uint32_t* scur;     // per node: store cursor of the current update
+  uint4* mv[2];       // mover lists: points that moved in the last advance round
   HSlot* hash;
   uint32_t* keys;     // backlog: table slots of this update's new cells
   uint8_t* data;
@@ -184,6 +194,7 @@ struct Ctx {
   uint32_t hash_mask;
   uint32_t max_nodes, max_chunks, spill_cap, backlog_cap, max_splits;
   uint64_t max_batch;
+  uint64_t mv_cap;  // entries of each mover list (batch + spill capacity)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -273,7 +284,8 @@ struct NodeCache {
   uint32_t n;  // cached nodes
 };
 
-// The whole block loads the cache (call after a grid/kernel boundary).
+// The whole block loads the cache and empties the block tally cache (call
+// after a grid/kernel boundary).
 __device__ __forceinline__ NodeCache load_node_cache(const Ctx& c, uint32_t* smem,
                                                      uint32_t n_nodes) {
   NodeCache nc;
@@ -284,8 +296,48 @@ __device__ __forceinline__ NodeCache load_node_cache(const Ctx& c, uint32_t* sme
     nc.child[i] = c.child[i];
     nc.grid[i] = c.gridref[i];
   }
+  for (uint32_t i = threadIdx.x; i < TALLY_SLOTS; i += blockDim.x) {
+    smem[SMEM_TALLY + i] = NONE;
+    smem[SMEM_TALLY + TALLY_SLOTS + i] = 0;
+  }
   __syncthreads();
   return nc;
+}
+
+// ------------------------------------------------------ block tally cache
+//
+// Per-update node counters (points counted into a leaf, new voxels of an
+// inner node) are summed per block in shared memory first: a direct-mapped
+// table of TALLY_SLOTS (node, count) pairs. A node whose slot holds another
+// node goes to the global counter at once. Dense regions send thousands of
+// warps to the same few counters; the cache turns their global atomics,
+// which serialise at one L2 slice, into one per block and node.
+
+__device__ __forceinline__ void tally_add(const Ctx& c, uint32_t* smem, uint32_t node,
+                                          uint32_t k) {
+#if SL_BLOCK_TALLY
+  const uint32_t slot = (node * 0x9E3779B1u) >> (32u - TALLY_LOG2);
+  uint32_t* tn = smem + SMEM_TALLY;
+  const uint32_t old = tn[slot] == node ? node : atomicCAS(tn + slot, NONE, node);
+  if (old == NONE || old == node) {
+    atomicAdd(tn + TALLY_SLOTS + slot, k);
+    return;
+  }
+#endif
+  atomicAdd(&c.cnt[node], k);
+}
+
+// The whole block calls at the end of a phase: add the cached counts to the
+// global counters.
+__device__ __forceinline__ void tally_flush(const Ctx& c, uint32_t* smem) {
+#if SL_BLOCK_TALLY
+  __syncthreads();
+  const uint32_t* tn = smem + SMEM_TALLY;
+  for (uint32_t i = threadIdx.x; i < TALLY_SLOTS; i += blockDim.x) {
+    const uint32_t node = tn[i], k = tn[TALLY_SLOTS + i];
+    if (node != NONE && k) atomicAdd(&c.cnt[node], k);
+  }
+#endif
 }
 
 __device__ __forceinline__ uint32_t node_child(const Ctx& c, NodeCache nc, uint32_t id) {
@@ -303,51 +355,62 @@ __device__ __forceinline__ T vload(const T* p) {
   return *reinterpret_cast<const volatile T*>(p);
 }
 
-// Lower the colour of a cell in the table to val (gidx << 32 | rgba) if val
-// is smaller. The result is not used, so the GPU does not wait for it.
-__device__ __forceinline__ void hash_lower(HSlot* s, unsigned long long val) {
-#if SL_CLAIM_READ_VAL
-  if (vload(&s->val) > val) atomicMin(&s->val, val);
-#else
-  atomicMin(&s->val, val);
-#endif
+// Key and value of a claim-table slot in one 16-byte load. Within an update
+// a slot's value only decreases once its key is set (the store phase empties
+// the slots between updates), so a value read with the key bounds the current
+// one from above.
+__device__ __forceinline__ ulonglong2 slot_load(const HSlot* s) {
+  ulonglong2 kv;
+  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];"
+               : "=l"(kv.x), "=l"(kv.y)
+               : "l"(s)
+               : "memory");
+  return kv;
 }
 
 // Probes after the first for `key` (slot h held another key): returns true,
 // with the slot in h, when this call put the key into the table (the cell is
-// new in this update); a slot already holding the key is lowered to val.
+// new in this update); a slot already holding the key is lowered to val if
+// val is smaller.
 __device__ bool hash_claim_rest(const Ctx& c, unsigned long long key, unsigned long long val,
                                 uint32_t& h) {
   for (int probe = 1; probe < MAX_PROBES; ++probe) {
     h = (h + 1u) & c.hash_mask;
     HSlot* s = c.hash + h;
-    unsigned long long k = vload(&s->key);
+    const ulonglong2 kv = slot_load(s);
+    unsigned long long k = kv.x;
     if (k == HASH_EMPTY) {
       k = atomicCAS(&s->key, HASH_EMPTY, key);
       if (k == HASH_EMPTY) {
         atomicMin(&s->val, val);
         return true;
       }
+      if (k == key) atomicMin(&s->val, val);
+      else continue;
+      return false;
     }
     if (k == key) {
-      hash_lower(s, val);
+      if (kv.y > val) atomicMin(&s->val, val);
       return false;
     }
   }
   set_error(c, E_BACKLOG);
   return false;
 }
+
 // Per-warp staging of the table slots of new cells (shared memory), flushed
 // to the backlog with one atomic per flush.
 struct WarpBuf {
-  uint32_t* buf;  // WBUF entries of this warp
-  uint32_t n;     // staged entries (the same value in every lane)
+  uint32_t* buf;   // WBUF entries of this warp
+  uint32_t n;      // staged entries (the same value in every lane)
+  uint32_t* smem;  // the block's dynamic shared memory (tally cache)
 };
 
 __device__ __forceinline__ WarpBuf warp_buf(uint32_t* smem) {
   WarpBuf wb;
-  wb.buf = smem + 2 * NODE_CACHE + (threadIdx.x / 32) * WBUF;
+  wb.buf = smem + SMEM_WBUF + (threadIdx.x / 32) * WBUF;
   wb.n = 0;
+  wb.smem = smem;
   return wb;
 }
 
@@ -367,57 +430,92 @@ __device__ __forceinline__ void warp_flush(const Ctx& c, WarpBuf& wb) {
   __syncwarp();
 }
 
-// All 32 lanes call. For each of N levels j, lanes with want[j] contend for
-// the cell key[j] = (node[j], cell) with val = (gidx << 32 | rgba); the lowest
-// gidx wins. Lanes with equal keys are merged first and only the lowest gidx
-// goes to the table. The first probes of all N levels are issued together
-// (their key loads, then their compare-and-swaps), so a descent pays about
-// two L2 round trips for all its claims. A key new in this update is staged
-// for the backlog and counted towards its node's new voxels.
+// Per-warp staging of mover-list entries (shared memory, after the node cache
+// and the new-cell staging), appended to the list with one atomicAdd per
+// flush: one reservation per MVBUF movers instead of one per warp unit.
+struct MoverBuf {
+  uint4* buf;
+  uint32_t n;  // staged entries (the same value in every lane)
+};
+
+__device__ __forceinline__ MoverBuf mover_buf(uint32_t* smem) {
+  MoverBuf mb;
+  mb.buf = reinterpret_cast<uint4*>(smem + SMEM_MVBUF) + (threadIdx.x / 32) * MVBUF;
+  mb.n = 0;
+  return mb;
+}
+
+// All 32 lanes call.
+__device__ __forceinline__ void mover_flush(const Ctx& c, MoverBuf& mb, int list) {
+  if (mb.n == 0u) return;
+  __syncwarp();
+  uint32_t o0 = 0;
+  if (lane_id() == 0) o0 = atomicAdd(&c.ctl->mv_count[list], mb.n);
+  o0 = __shfl_sync(FULL_MASK, o0, 0);
+  for (uint32_t k = lane_id(); k < mb.n; k += 32) {
+    const uint64_t o = (uint64_t)o0 + k;
+    if (o < c.mv_cap) c.mv[list][o] = mb.buf[k];
+    else set_error(c, E_INTERNAL);
+  }
+  mb.n = 0;
+  __syncwarp();
+}
+
+// All 32 lanes call: lanes with `moved` stage entry `ent`.
+__device__ __forceinline__ void mover_add(const Ctx& c, MoverBuf& mb, int list, bool moved,
+                                          uint4 ent) {
+  const unsigned mm = __ballot_sync(FULL_MASK, moved);
+  if (mm == 0u) return;
+  const uint32_t k = (uint32_t)__popc(mm);
+  if (mb.n + k > MVBUF) mover_flush(c, mb, list);
+  if (moved) mb.buf[mb.n + __popc(mm & ((1u << lane_id()) - 1u))] = ent;
+  mb.n += k;
+}
+
+// All 32 lanes call. Lanes with lead[j] offer val[j] for cell key[j] of node
+// node[j] to the update's claim table; the lowest value wins. The first
+// probes of all N items are issued together (their key loads, then their
+// compare-and-swaps), so the items pay about two L2 round trips together. A
+// key new in this update is staged for the backlog and counted towards its
+// node's new voxels.
 template <int N>
-__device__ __forceinline__ void warp_claim(const Ctx& c, WarpBuf& wb, const bool (&want)[N],
-                                           const unsigned long long (&key)[N],
-                                           const uint32_t (&gidx)[N], const uint32_t (&rgba)[N],
-                                           const uint32_t (&node)[N]) {
+__device__ __forceinline__ void warp_claim_global(const Ctx& c, WarpBuf& wb, const bool (&lead)[N],
+                                                  const unsigned long long (&key)[N],
+                                                  const unsigned long long (&val)[N],
+                                                  const uint32_t (&node)[N]) {
   const uint32_t lane = lane_id();
-  bool any = false;
-#pragma unroll
-  for (int j = 0; j < N; ++j) any = any || want[j];
-  if (__ballot_sync(FULL_MASK, any) == 0u) return;
-  bool lead[N], cas[N], inst[N];
+  bool cas[N], inst[N];
   uint32_t h[N];
-  unsigned long long k0[N];
+  unsigned long long k0[N], v0[N];
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    const unsigned m = __ballot_sync(FULL_MASK, want[j]);
-    lead[j] = false;
-    if (want[j]) {
-      const unsigned grp = __match_any_sync(m, key[j]);
-      lead[j] = __reduce_min_sync(grp, gidx[j]) == gidx[j];
+    h[j] = (uint32_t)fmix64(key[j]) & c.hash_mask;
+    k0[j] = v0[j] = 0ull;
+    if (lead[j]) {
+      const ulonglong2 kv = slot_load(c.hash + h[j]);
+      k0[j] = kv.x;
+      v0[j] = kv.y;
     }
   }
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    h[j] = (uint32_t)fmix64(key[j]) & c.hash_mask;
-    k0[j] = lead[j] ? vload(&c.hash[h[j]].key) : 0ull;
-  }
-#pragma unroll
-  for (int j = 0; j < N; ++j) {
     cas[j] = lead[j] && k0[j] == HASH_EMPTY;
-    if (cas[j]) k0[j] = atomicCAS(&c.hash[h[j]].key, HASH_EMPTY, key[j]);
+    if (cas[j]) {
+      k0[j] = atomicCAS(&c.hash[h[j]].key, HASH_EMPTY, key[j]);
+      v0[j] = HASH_EMPTY;
+    }
   }
 #pragma unroll
   for (int j = 0; j < N; ++j) {
     inst[j] = false;
-    const unsigned long long val = ((unsigned long long)gidx[j] << 32) | rgba[j];
     if (lead[j]) {
       if (cas[j] && k0[j] == HASH_EMPTY) {
         inst[j] = true;
-        atomicMin(&c.hash[h[j]].val, val);
+        atomicMin(&c.hash[h[j]].val, val[j]);
       } else if (k0[j] == key[j]) {
-        hash_lower(c.hash + h[j], val);
+        if (v0[j] > val[j]) atomicMin(&c.hash[h[j]].val, val[j]);
       } else {
-        inst[j] = hash_claim_rest(c, key[j], val, h[j]);
+        inst[j] = hash_claim_rest(c, key[j], val[j], h[j]);
       }
     }
   }
@@ -430,19 +528,48 @@ __device__ __forceinline__ void warp_claim(const Ctx& c, WarpBuf& wb, const bool
     if (inst[j]) {
       wb.buf[wb.n + __popc(mi & ((1u << lane) - 1u))] = h[j];
       const unsigned gm = __match_any_sync(mi, node[j]);
-      if ((int)lane == __ffs(gm) - 1) atomicAdd(&c.cnt[node[j]], (uint32_t)__popc(gm));
+      if ((int)lane == __ffs(gm) - 1) tally_add(c, wb.smem, node[j], (uint32_t)__popc(gm));
     }
     wb.n += ni;
   }
 }
 
+// All 32 lanes call. For each of N items j, lanes with want[j] contend for
+// the cell key[j] = (node[j], cell) with val = (gidx << 32 | rgba); the lowest
+// gidx wins. Lanes with equal keys are merged first and only the lowest gidx
+// goes to the global table.
+template <int N>
+__device__ __forceinline__ void warp_claim(const Ctx& c, WarpBuf& wb, const bool (&want)[N],
+                                           const unsigned long long (&key)[N],
+                                           const uint32_t (&gidx)[N], const uint32_t (&rgba)[N],
+                                           const uint32_t (&node)[N]) {
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < N; ++j) any = any || want[j];
+  if (__ballot_sync(FULL_MASK, any) == 0u) return;
+  bool lead[N];
+  unsigned long long val[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const unsigned m = __ballot_sync(FULL_MASK, want[j]);
+    lead[j] = false;
+    val[j] = ((unsigned long long)gidx[j] << 32) | rgba[j];
+    if (want[j]) {
+      const unsigned grp = __match_any_sync(m, key[j]);
+      lead[j] = __reduce_min_sync(grp, gidx[j]) == gidx[j];
+    }
+  }
+  warp_claim_global<N>(c, wb, lead, key, val, node);
+}
+
 // All 32 lanes call. Lanes with `valid` count one point into `leaf` (a
 // reduction per distinct leaf of the warp; the slot is given at store).
-__device__ __forceinline__ void warp_tally(const Ctx& c, bool valid, uint32_t leaf) {
+__device__ __forceinline__ void warp_tally(const Ctx& c, uint32_t* smem, bool valid,
+                                           uint32_t leaf) {
   const unsigned m = __ballot_sync(FULL_MASK, valid);
   if (valid) {
     const unsigned grp = __match_any_sync(m, leaf);
-    if ((int)lane_id() == __ffs(grp) - 1) atomicAdd(&c.cnt[leaf], (uint32_t)__popc(grp));
+    if ((int)lane_id() == __ffs(grp) - 1) tally_add(c, smem, leaf, (uint32_t)__popc(grp));
   }
 }
 
@@ -534,28 +661,26 @@ __device__ void phase_count1(const Ctx& c, uint32_t* smem, uint32_t n_nodes, con
       }
       warp_claim<DESCENT_GROUP>(c, wb, want, key, gg, gc, gnode);
     }
-    warp_tally(c, valid, node);
+    warp_tally(c, smem, valid, node);
     if (valid) c.b_cur[i] = node;
   }
   warp_flush(c, wb);
+  tally_flush(c, smem);
 }
 
 // ----------------------------------------------------------- phase: advance
 
-constexpr int ADV_U = SL_ADVANCE_UNROLL;
-
 // U items per lane whose cursor node split in the previous round (moving[j]:
-// the cursor cur[j] has children) sample that node's grid (empty until store,
-// so every point contends) and move one level down, counting into the child.
-// cur[j] then holds the new cursor.
+// the cursor cur[j], at level lvl[j], has children ch[j]) sample that node's
+// grid (empty until store, so every point contends) and move one level down,
+// counting into the child. cur[j] then holds the new cursor.
 template <int U>
 __device__ __forceinline__ void advance_items(const Ctx& c, WarpBuf& wb, const bool (&moving)[U],
                                               const int4 (&p)[U], const uint32_t (&gidx)[U],
-                                              const uint32_t (&ch)[U], uint32_t (&cur)[U]) {
-  uint32_t lvl[U], nxt[U], rgba[U];
+                                              const uint32_t (&lvl)[U], const uint32_t (&ch)[U],
+                                              uint32_t (&cur)[U]) {
+  uint32_t nxt[U], rgba[U];
   unsigned long long key[U];
-#pragma unroll
-  for (int j = 0; j < U; ++j) lvl[j] = moving[j] ? c.meta[cur[j]].level : 0u;
 #pragma unroll
   for (int j = 0; j < U; ++j) {
     uint32_t rx = 0, ry = 0, rz = 0, cell = 0;
@@ -572,24 +697,37 @@ __device__ __forceinline__ void advance_items(const Ctx& c, WarpBuf& wb, const b
   warp_claim<U>(c, wb, moving, key, gidx, rgba, cur);
 #pragma unroll
   for (int j = 0; j < U; ++j) {
-    warp_tally(c, moving[j], nxt[j]);
+    warp_tally(c, wb.smem, moving[j], nxt[j]);
     cur[j] = nxt[j];
   }
 }
 
-// Round of the expansion after the first: zero the grids of the splits
-// [s_lo, s_hi) of the previous round, then move the batch points and the
-// points of the spill tasks [0, t_hi) (tasks [t_lo, t_hi) are new: their
-// points still sit at the split leaf) whose cursor node split. Points are
-// cut into 32-item warp units (a unit of a task never crosses into the next
-// task); each warp takes U units at a time so that their L2 round trips
-// overlap.
+// A mover-list entry (16 bytes) is a point whose cursor moved in the last
+// advance round: x = MV_SPILL | spill entry, or a batch point index; y = its
+// cursor node; z = that node's level.
+constexpr uint32_t MV_SPILL = 1u << 31;
+
+// Advance round r of the expansion (r >= 2 counts decide rounds): zero the
+// grids of the splits [s_lo, s_hi) of the previous decide, then move every
+// point whose cursor node split there one level down (advance_items), and
+// list the points that moved in mover list out_list.
+//
+// Only nodes created in the previous round can split in a later one (every
+// leaf that existed before the update was decided in the first round), so
+// only points that moved in the previous round can move again: the first
+// round (in_list < 0) scans every batch cursor and every point of the spill
+// tasks [0, t_hi) (all created by the first decide; their points still sit
+// in the split leaf's chunks and are copied to the spill records here), later
+// rounds only the n_in entries of mover list in_list, which carry cursor and
+// level. Points are cut into 32-item warp units (a unit of a task never
+// crosses into the next task).
 __device__ void phase_advance(const Ctx& c, uint32_t* smem, uint32_t n_nodes, const int4* pts,
-                              uint64_t n, unsigned long long base, uint32_t t_lo, uint32_t t_hi,
-                              uint32_t s_lo, uint32_t s_hi, uint64_t warp0, uint64_t nwarps) {
-  constexpr int U = ADV_U;
+                              uint64_t n, unsigned long long base, uint32_t t_hi, uint32_t s_lo,
+                              uint32_t s_hi, int in_list, uint32_t n_in, int out_list,
+                              uint64_t warp0, uint64_t nwarps) {
   const NodeCache nc = load_node_cache(c, smem, n_nodes);
   WarpBuf wb = warp_buf(smem);
+  MoverBuf mb = mover_buf(smem);
   const uint32_t lane = lane_id();
   const uint32_t zpg = (c.grid_bytes + ZERO_UNIT - 1) / ZERO_UNIT;  // zero units per grid
   const uint64_t uz = (uint64_t)(s_hi - s_lo) * zpg;
@@ -606,69 +744,89 @@ __device__ void phase_advance(const Ctx& c, uint32_t* smem, uint32_t n_nodes, co
     for (uint32_t b = lo / 16 + lane; b < hi / 16; b += 32) g[b] = make_int4(0, 0, 0, 0);
   }
   const uint32_t parts = (c.C + 31) / 32;  // units per task
-  const uint64_t ub = (n + 31) / 32;
-  const uint64_t units = ub + (uint64_t)t_hi * parts;
-  for (uint64_t w0 = warp0; w0 < units; w0 += U * nwarps) {
-    bool valid[U], moving[U], spill[U];
-    uint32_t cur[U], ch[U], gidx[U], src[U], e[U];
-    int4 p[U];
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      const uint64_t w = w0 + j * nwarps;
-      spill[j] = w >= ub;
-      valid[j] = false;
-      cur[j] = 0;
-      src[j] = NONE;
-      e[j] = 0;
-      gidx[j] = 0;
-      if (w < ub) {
-        const uint64_t i = w * 32 + lane;
-        valid[j] = i < n;
-        cur[j] = valid[j] ? c.b_cur[i] : 0u;
-        gidx[j] = (uint32_t)(base + i);
-        e[j] = (uint32_t)i;
-      } else if (w < units) {
-        const uint64_t u = w - ub;
-        const uint32_t t = (uint32_t)(u / parts), q = (uint32_t)(u % parts) * 32u + lane;
-        const SpillTask tk = c.tasks[t];
-        const bool task_ok = ref_ok(c, tk.ref, c.chunk_bytes) && tk.n <= c.C &&
-                             (unsigned long long)tk.dst + tk.n <= c.spill_cap;
-        if (!task_ok && lane == 0) set_error(c, E_INTERNAL);
-        valid[j] = task_ok && q < tk.n;
-        e[j] = tk.dst + q;
-        src[j] = tk.ref;
-        gidx[j] = q;  // index in the chunk until the point is read
-        cur[j] = valid[j] ? (t >= t_lo ? tk.node : c.sp_cur[e[j]]) : 0u;
+  const bool first = in_list < 0;
+  const uint64_t ub = first ? (n + 31) / 32 : 0;
+  const uint64_t units = first ? ub + (uint64_t)t_hi * parts : ((uint64_t)n_in + 31) / 32;
+  const uint4* in = first ? nullptr : c.mv[in_list];
+  for (uint64_t w = warp0; w < units; w += nwarps) {
+    bool valid = false, spill = false;
+    uint32_t idx = 0;  // batch point index or spill entry
+    uint32_t cur = 0, lvl = 0;
+    int4 p = make_int4(0, 0, 0, 0);
+    uint32_t g = 0;
+    bool have_p = false;
+    if (first && w < ub) {
+      const uint64_t i = w * 32 + lane;
+      valid = i < n;
+      idx = (uint32_t)i;
+      cur = valid ? c.b_cur[i] : 0u;
+    } else if (first) {
+      const uint64_t u = w - ub;
+      const uint32_t t = (uint32_t)(u / parts), q = (uint32_t)(u % parts) * 32u + lane;
+      const SpillTask tk = c.tasks[t];
+      const bool task_ok = ref_ok(c, tk.ref, c.chunk_bytes) && tk.n <= c.C &&
+                           (unsigned long long)tk.dst + tk.n <= c.spill_cap;
+      if (!task_ok && lane == 0) set_error(c, E_INTERNAL);
+      valid = task_ok && q < tk.n;
+      spill = true;
+      idx = tk.dst + q;
+      cur = tk.node;
+      if (valid) {
+        // the point leaves its chunk (which returns to the pool at store)
+        p = chunk_recs(c, tk.ref)[q];
+        g = chunk_aux(c, tk.ref)[q];
+        c.sp_rec[idx] = p;
+        c.sp_gidx[idx] = g;
+        have_p = true;
       }
-    }
-    // read a point only when its cursor node split (it moves)
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      if (valid[j] && cur[j] >= c.max_nodes) {
-        set_error(c, E_INTERNAL);
-        valid[j] = false;
-      }
-      ch[j] = valid[j] ? node_child(c, nc, cur[j]) : NONE;
-      moving[j] = ch[j] != NONE && ch[j] + 8u <= c.max_nodes;
-      p[j] = make_int4(0, 0, 0, 0);
-      if (moving[j]) {
-        if (spill[j]) {
-          p[j] = chunk_recs(c, src[j])[gidx[j]];
-          gidx[j] = chunk_aux(c, src[j])[gidx[j]];
-        } else {
-          p[j] = __ldg(pts + e[j]);
+    } else {
+      const uint64_t k = w * 32 + lane;
+      if (k < n_in) {
+        const uint4 ent = in[k];
+        valid = true;
+        spill = (ent.x & MV_SPILL) != 0u;
+        idx = ent.x & ~MV_SPILL;
+        cur = ent.y;
+        lvl = ent.z;
+        if (spill ? idx >= c.spill_cap : idx >= n) {
+          set_error(c, E_INTERNAL);
+          valid = false;
         }
       }
     }
-    advance_items<U>(c, wb, moving, p, gidx, ch, cur);
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      if (!moving[j]) continue;
-      if (spill[j]) c.sp_cur[e[j]] = cur[j];
-      else c.b_cur[e[j]] = cur[j];
+    if (valid && cur >= c.max_nodes) {
+      set_error(c, E_INTERNAL);
+      valid = false;
     }
+    // read a point only when its cursor node split (it moves)
+    const uint32_t ch0 = valid ? node_child(c, nc, cur) : NONE;
+    const bool mv0 = ch0 != NONE && ch0 + 8u <= c.max_nodes;
+    if (mv0) {
+      if (first) lvl = c.meta[cur].level;
+      if (!have_p) {
+        if (spill) {
+          p = c.sp_rec[idx];
+          g = c.sp_gidx[idx];
+        } else {
+          p = __ldg(pts + idx);
+          g = (uint32_t)(base + idx);
+        }
+      }
+    }
+    const bool moving[1] = {mv0};
+    const int4 pp[1] = {p};
+    const uint32_t gidx[1] = {g}, lv[1] = {lvl}, ch[1] = {ch0};
+    uint32_t cr[1] = {cur};
+    advance_items<1>(c, wb, moving, pp, gidx, lv, ch, cr);
+    if (mv0) {
+      if (spill) c.sp_cur[idx] = cr[0];
+      else c.b_cur[idx] = cr[0];
+    }
+    mover_add(c, mb, out_list, mv0, make_uint4(spill ? (idx | MV_SPILL) : idx, cr[0], lvl + 1u, 0u));
   }
   warp_flush(c, wb);
+  mover_flush(c, mb, out_list);
+  tally_flush(c, smem);
 }
 
 // ------------------------------------------------------------ phase: decide
@@ -856,9 +1014,12 @@ __device__ __forceinline__ void decide_node(const Ctx& c, uint32_t id) {
 
 // Candidates, one warp each: the nodes split in the previous round (their
 // voxels are now all claimed) and the node id range [n_lo, n_hi).
+// zero_list >= 0: also empty that mover list (the next advance round fills
+// it; the round before last was its reader).
 __device__ void phase_decide(const Ctx& c, uint32_t s_lo, uint32_t s_hi, uint32_t n_lo,
-                             uint32_t n_hi, uint64_t warp0, uint64_t nwarps) {
+                             uint32_t n_hi, int zero_list, uint64_t warp0, uint64_t nwarps) {
   const uint64_t ns = s_hi - s_lo, nn = n_hi - n_lo;
+  if (zero_list >= 0 && warp0 == 0 && lane_id() == 0) c.ctl->mv_count[zero_list] = 0;
   for (uint64_t w = warp0; w < ns + nn; w += nwarps) {
     const uint32_t id = w < ns ? c.splits[s_lo + w].node : (uint32_t)(n_lo + (w - ns));
     decide_node(c, id);
@@ -948,15 +1109,15 @@ __device__ __forceinline__ void put_rec(const Ctx& c, uint32_t ref, uint32_t q, 
 
 constexpr int STORE_U = SL_STORE_UNROLL;
 
-// Store the batch points, the re-inserted points of the spill tasks [0,
-// n_tasks) and the n_keys new voxels, each at the next free slot of its node;
-// hand the chunks of split leaves (one per task) to the pool above pool_top
-// (the caller then raises pool_top). Loops are warp-uniform so that the
+// Store the batch points, the n_spill re-inserted points (from the spill
+// records) and the n_keys new voxels, each at the next free slot of its node;
+// hand the n_tasks chunks of split leaves (one per task) to the pool above
+// pool_top (the caller then raises pool_top). Loops are warp-uniform so that the
 // lanes of a warp share one slot reservation per node; each lane carries
 // STORE_U items at a time so that their L2 round trips overlap.
 __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned long long base,
-                            uint32_t n_tasks, uint32_t n_keys, int pool_top, uint64_t t0,
-                            uint64_t nthreads) {
+                            uint32_t n_spill, uint32_t n_tasks, uint32_t n_keys, int pool_top,
+                            uint64_t t0, uint64_t nthreads) {
   constexpr int U = STORE_U;
   const uint32_t lane = lane_id();
   const uint64_t w0 = t0 - lane, wstride = nthreads;  // warp-aligned start and stride
@@ -979,36 +1140,21 @@ __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned 
 #pragma unroll
     for (int j = 0; j < U; ++j) put_rec(c, ref[j], q[j], p[j], (uint32_t)(base + b0 + j * wstride + lane));
   }
-  const uint64_t tp = (uint64_t)n_tasks * c.C;
-  for (uint64_t b0 = w0; b0 < tp; b0 += U * wstride) {
+  for (uint64_t b0 = w0; b0 < n_spill; b0 += U * wstride) {
     bool valid[U];
-    uint32_t node[U], ref[U], q[U], src[U], qs[U];
+    uint32_t node[U], ref[U], q[U], g[U];
+    int4 r[U];
 #pragma unroll
     for (int j = 0; j < U; ++j) {
-      const uint64_t u = b0 + j * wstride + lane;
-      valid[j] = u < tp;
-      const uint32_t t = valid[j] ? (uint32_t)(u / c.C) : 0u;
-      qs[j] = valid[j] ? (uint32_t)(u - (uint64_t)t * c.C) : 0u;
-      const SpillTask tk = valid[j] ? c.tasks[t] : SpillTask{NONE, 0, 0, 0};
-      valid[j] = valid[j] && qs[j] < tk.n;
-      if (valid[j] && (!ref_ok(c, tk.ref, c.chunk_bytes) ||
-                       (unsigned long long)tk.dst + tk.n > c.spill_cap)) {
-        set_error(c, E_INTERNAL);
-        valid[j] = false;
-      }
-      src[j] = tk.ref;
-      node[j] = valid[j] ? c.sp_cur[tk.dst + qs[j]] : 0u;
+      const uint64_t e = b0 + j * wstride + lane;
+      valid[j] = e < n_spill;
+      node[j] = valid[j] ? c.sp_cur[e] : 0u;
+      r[j] = valid[j] ? c.sp_rec[e] : make_int4(0, 0, 0, 0);
+      g[j] = valid[j] ? c.sp_gidx[e] : 0u;
       if (valid[j] && node[j] >= c.max_nodes) {
         set_error(c, E_INTERNAL);
         valid[j] = false;
       }
-    }
-    int4 r[U];
-    uint32_t g[U];
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      r[j] = valid[j] ? chunk_recs(c, src[j])[qs[j]] : make_int4(0, 0, 0, 0);
-      g[j] = valid[j] ? chunk_aux(c, src[j])[qs[j]] : 0u;
     }
     warp_place<U>(c, valid, node, ref, q);
 #pragma unroll
@@ -1093,6 +1239,8 @@ __device__ void phase_end(const Ctx& c, uint64_t n, uint32_t iters) {
   t->alloc_seq = 0;
   t->split_count = 0;
   t->ntasks = 0;
+  t->mv_count[0] = 0;
+  t->mv_count[1] = 0;
 }
 
 // One thread: close a rejected update (the rollback undid its counters).

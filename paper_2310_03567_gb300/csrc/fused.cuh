@@ -135,14 +135,17 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
         }
       } else {
         // s: split-list range of the previous round, n: nodes it created,
-        // t: its spill tasks (tasks below t_lo are older)
-        uint32_t s_lo = 0, s_hi = 0, n_lo = 0, n_hi = nodes0, t_lo = 0, t_hi = 0, iters = 1;
+        // t_hi: spill tasks (all made by the first decide round)
+        uint32_t s_lo = 0, s_hi = 0, n_lo = 0, n_hi = nodes0, t_hi = 0, iters = 1;
         for (;;) {
-          phase_decide(c, s_lo, s_hi, n_lo, n_hi, warp0, nwarps);
+          phase_decide(c, s_lo, s_hi, n_lo, n_hi, iters >= 3 ? (int)((iters - 1) & 1u) : -1,
+                       warp0, nwarps);
           if (!grid_barrier(c, f)) return;
           clk.tick(c, PH_DECIDE);
           const uint32_t sc = vload(&c.ctl->split_count), nn = vload(&c.ctl->n_nodes);
           const uint32_t nt = vload(&c.ctl->ntasks);
+          if (iters == 1) t_hi = nt;
+          else if (nt != t_hi && tid == 0) set_error(c, E_INTERNAL);
           if (sc == s_hi) break;
           if (iters >= max_iters) {
             if (tid == 0) set_error(c, E_ITER_CAP);
@@ -152,17 +155,19 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
           s_hi = sc;
           n_lo = n_hi;
           n_hi = nn;
-          t_lo = t_hi;
-          t_hi = nt;
+          const int in_list = iters >= 2 ? (int)((iters - 2) & 1u) : -1;
+          const uint32_t n_in = in_list >= 0 ? vload(&c.ctl->mv_count[in_list]) : 0u;
+          phase_advance(c, smem, nn, bd.pts, bd.n, base, t_hi, s_lo, s_hi, in_list, n_in,
+                        (int)((iters - 1) & 1u), warp0, nwarps);
           ++iters;
-          phase_advance(c, smem, nn, bd.pts, bd.n, base, t_lo, t_hi, s_lo, s_hi, warp0, nwarps);
           if (!grid_barrier(c, f)) return;
           clk.tick(c, PH_ADVANCE);
         }
         const uint32_t n_tasks = vload(&c.ctl->ntasks);
+        const uint32_t n_spill = min(vload(&c.ctl->spill_count), c.spill_cap);
         const uint32_t n_keys = min(vload(&c.ctl->nkeys), c.backlog_cap);
         const int pool_top = vload(&c.ctl->pool_top);
-        phase_store(c, bd.pts, bd.n, base, n_tasks, n_keys, pool_top, tid, nthreads);
+        phase_store(c, bd.pts, bd.n, base, n_spill, n_tasks, n_keys, pool_top, tid, nthreads);
         if (!grid_barrier(c, f)) return;
         clk.tick(c, PH_STORE);
         if (tid == 0) phase_end(c, bd.n, iters);

@@ -66,31 +66,31 @@ __global__ void __launch_bounds__(PBLOCK, PHASE_MIN_BLOCKS) k_count1(Ctx c, cons
 // Decide / allocate; after the first count round of a rejected batch (no
 // thread changes the reject flag during this kernel) undo that round instead.
 __global__ void __launch_bounds__(BLOCK) k_decide(Ctx c, uint32_t s_lo, uint32_t s_hi,
-                                                   uint32_t n_lo, uint32_t n_hi) {
+                                                   uint32_t n_lo, uint32_t n_hi, int zero_list) {
   const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
   if (*reinterpret_cast<volatile unsigned int*>(&c.ctl->reject)) {
     phase_rollback(c, n_hi, t0, nt);
     return;
   }
-  phase_decide(c, s_lo, s_hi, n_lo, n_hi, t0 / 32, nt / 32);
+  phase_decide(c, s_lo, s_hi, n_lo, n_hi, zero_list, t0 / 32, nt / 32);
 }
 
 __global__ void __launch_bounds__(PBLOCK, PHASE_MIN_BLOCKS) k_advance(Ctx c, const int4* pts, uint64_t n,
                                                      unsigned long long base, uint32_t n_nodes,
-                                                     uint32_t t_lo, uint32_t t_hi, uint32_t s_lo,
-                                                     uint32_t s_hi) {
+                                                     uint32_t t_hi, uint32_t s_lo, uint32_t s_hi,
+                                                     int in_list, uint32_t n_in, int out_list) {
   extern __shared__ uint32_t smem[];
   const uint64_t warps_per_block = blockDim.x / 32;
-  phase_advance(c, smem, n_nodes, pts, n, base, t_lo, t_hi, s_lo, s_hi,
+  phase_advance(c, smem, n_nodes, pts, n, base, t_hi, s_lo, s_hi, in_list, n_in, out_list,
                 blockIdx.x * warps_per_block + threadIdx.x / 32,
                 (uint64_t)gridDim.x * warps_per_block);
 }
 
 __global__ void __launch_bounds__(BLOCK) k_store(Ctx c, const int4* pts, uint64_t n,
-                                                  unsigned long long base, uint32_t n_tasks,
-                                                  uint32_t n_keys, int pool_top) {
-  phase_store(c, pts, n, base, n_tasks, n_keys, pool_top,
+                                                  unsigned long long base, uint32_t n_spill,
+                                                  uint32_t n_tasks, uint32_t n_keys, int pool_top) {
+  phase_store(c, pts, n, base, n_spill, n_tasks, n_keys, pool_top,
               blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
 
@@ -108,7 +108,7 @@ static const char* const kKernelNames[SIMLOD_N_KERNELS] = {
 
 struct Layout {
   size_t ctl, fctl, batches, child, gridref, cnt, num, meta, pool, pending, alloc_refs, splits,
-      tasks, sp_cur, b_cur, scur, hash, keys, staging, data, end;
+      tasks, sp_cur, sp_rec, sp_gidx, b_cur, mv0, mv1, scur, hash, keys, staging, data, end;
   uint64_t hash_slots, max_chunks, max_splits, data_bytes;
 };
 
@@ -161,8 +161,9 @@ bool valid_config(const simlod_config* c) {
   if (c->root_log2 < 1 || c->root_log2 > 31) return false;
   if (c->leaf_capacity < 1 || c->chunk_points < 1 || c->chunk_points > 65536) return false;
   if (c->grid_log2 < 1 || c->grid_log2 > 7) return false;
-  if (c->max_batch_points < 1 || c->max_batch_points > (1ull << 32)) return false;
-  if (c->spill_capacity > 0xFFFFFFFFull || c->backlog_capacity < 1 ||
+  // mover-list entries name a batch point or a spill entry in 31 bits
+  if (c->max_batch_points < 1 || c->max_batch_points >= (1ull << 31)) return false;
+  if (c->spill_capacity >= (1ull << 31) || c->backlog_capacity < 1 ||
       c->backlog_capacity > (1ull << 31))
     return false;
   if (c->max_nodes < 9 || c->max_nodes > (1ull << 31)) return false;
@@ -217,6 +218,10 @@ bool plan_layout(const simlod_config* c, size_t arena_bytes, Layout* L) {
   L->splits = take(sizeof(SplitEntry) * L->max_splits);
   L->sp_cur = take(4 * S);
   L->b_cur = take(4 * B);
+  L->mv0 = take(16 * (B + S));
+  L->mv1 = take(16 * (B + S));
+  L->sp_rec = take(16 * S);
+  L->sp_gidx = take(4 * S);
   L->scur = take(4 * N);
   L->hash = take(sizeof(HSlot) * L->hash_slots);
   L->keys = take(sizeof(uint32_t) * c->backlog_capacity);
@@ -259,6 +264,10 @@ void make_ctx(simlod_t* h) {
   c.tasks = reinterpret_cast<SpillTask*>(a + L.tasks);
   c.sp_cur = reinterpret_cast<uint32_t*>(a + L.sp_cur);
   c.b_cur = reinterpret_cast<uint32_t*>(a + L.b_cur);
+  c.mv[0] = reinterpret_cast<uint4*>(a + L.mv0);
+  c.mv[1] = reinterpret_cast<uint4*>(a + L.mv1);
+  c.sp_rec = reinterpret_cast<int4*>(a + L.sp_rec);
+  c.sp_gidx = reinterpret_cast<uint32_t*>(a + L.sp_gidx);
   c.scur = reinterpret_cast<uint32_t*>(a + L.scur);
   c.hash = reinterpret_cast<HSlot*>(a + L.hash);
   c.keys = reinterpret_cast<uint32_t*>(a + L.keys);
@@ -283,6 +292,7 @@ void make_ctx(simlod_t* h) {
   c.backlog_cap = (uint32_t)g.backlog_capacity;
   c.max_splits = (uint32_t)L.max_splits;
   c.max_batch = g.max_batch_points;
+  c.mv_cap = g.max_batch_points + g.spill_capacity;
 }
 
 int error_from_bits(uint32_t e) {
@@ -383,7 +393,7 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
   });
   if (rc) return poison(h, rc);
   rc = launch(h, K_DECIDE, s, [&] {
-    k_decide<<<grid_for(h, 32ull * nodes0, BLOCK), BLOCK, 0, s>>>(c, 0, 0, 0, nodes0);
+    k_decide<<<grid_for(h, 32ull * nodes0, BLOCK), BLOCK, 0, s>>>(c, 0, 0, 0, nodes0, -1);
   });
   if (rc) return poison(h, rc);
   if ((rc = read_ctl(h, s))) return poison(h, rc);
@@ -397,41 +407,50 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
   const uint32_t max_iters = h->cfg.max_expand_iters ? h->cfg.max_expand_iters
                                                       : h->cfg.root_log2 + 1;
   // s: split-list range of the previous round, n: nodes it created,
-  // t: its spill tasks (tasks below t_lo are older)
-  uint32_t s_lo = 0, s_hi = t.split_count, n_lo = nodes0, n_hi = t.n_nodes, t_lo = 0,
+  // t_hi: spill tasks (all made by the first decide round)
+  uint32_t s_lo = 0, s_hi = t.split_count, n_lo = nodes0, n_hi = t.n_nodes,
            t_hi = t.ntasks, iters = 1;
   while (s_hi > s_lo) {
     if (iters >= max_iters) return poison(h, SIMLOD_ERR_ITER_CAP);
-    const uint64_t units = (n + 31) / 32 + (uint64_t)t_hi * 8 + (uint64_t)(s_hi - s_lo) * 64;
+    const int in_list = iters >= 2 ? (int)((iters - 2) & 1u) : -1;
+    const int out_list = (int)((iters - 1) & 1u);
+    const uint32_t n_in = in_list >= 0 ? h->ctl_host->mv_count[in_list] : 0u;
+    const uint64_t units = (in_list < 0 ? (n + 31) / 32 + (uint64_t)t_hi * ((c.C + 31) / 32)
+                                        : ((uint64_t)n_in + 31) / 32) +
+                           (uint64_t)(s_hi - s_lo) * 64;
     const unsigned ga =
         std::max(1u, std::min<unsigned>(grid_for(h, units * 32, PBLOCK), (unsigned)PHASE_MIN_BLOCKS * h->sm_count));
     const uint32_t nn = n_hi;
     rc = launch(h, K_ADVANCE, s, [&] {
-      k_advance<<<ga, PBLOCK, PHASE_SMEM_BYTES, s>>>(c, pts, n, base, nn, t_lo, t_hi, s_lo, s_hi);
+      k_advance<<<ga, PBLOCK, PHASE_SMEM_BYTES, s>>>(c, pts, n, base, nn, t_hi, s_lo, s_hi,
+                                                     in_list, n_in, out_list);
     });
     if (rc) return poison(h, rc);
+    ++iters;
     const uint64_t cand = (uint64_t)(s_hi - s_lo) + (n_hi - n_lo);
+    const int zero_list = iters >= 3 ? (int)((iters - 1) & 1u) : -1;
     rc = launch(h, K_DECIDE, s, [&] {
-      k_decide<<<grid_for(h, 32 * cand, BLOCK), BLOCK, 0, s>>>(c, s_lo, s_hi, n_lo, n_hi);
+      k_decide<<<grid_for(h, 32 * cand, BLOCK), BLOCK, 0, s>>>(c, s_lo, s_hi, n_lo, n_hi,
+                                                              zero_list);
     });
     if (rc) return poison(h, rc);
     if ((rc = read_ctl(h, s))) return poison(h, rc);
     if (h->ctl_host->error) return poison(h, error_from_bits(h->ctl_host->error));
+    if (h->ctl_host->ntasks != t_hi) return poison(h, SIMLOD_ERR_CUDA);
     s_lo = s_hi;
     s_hi = h->ctl_host->split_count;
     n_lo = n_hi;
     n_hi = h->ctl_host->n_nodes;
-    t_lo = t_hi;
-    t_hi = h->ctl_host->ntasks;
-    ++iters;
   }
   const uint32_t n_tasks = h->ctl_host->ntasks;
+  const uint32_t n_spill = std::min<uint32_t>(h->ctl_host->spill_count, c.spill_cap);
   const uint32_t n_keys = std::min<uint32_t>(h->ctl_host->nkeys, c.backlog_cap);
   const int pool_top = h->ctl_host->pool_top;
-  const uint64_t work = std::max<uint64_t>(std::max<uint64_t>(n, (uint64_t)n_tasks * c.C), n_keys);
+  const uint64_t work =
+      std::max<uint64_t>(std::max<uint64_t>(std::max<uint64_t>(n, n_spill), n_tasks), n_keys);
   rc = launch(h, K_STORE, s, [&] {
-    k_store<<<grid_for(h, work, BLOCK), BLOCK, 0, s>>>(c, pts, n, base, n_tasks, n_keys,
-                                                      pool_top);
+    k_store<<<grid_for(h, work, BLOCK), BLOCK, 0, s>>>(c, pts, n, base, n_spill, n_tasks,
+                                                      n_keys, pool_top);
   });
   if (rc) return poison(h, rc);
   rc = launch(h, K_END, s, [&] { k_end<<<1, 1, 0, s>>>(c, n, iters); });

@@ -1,0 +1,39 @@
+"""Parity at the full benchmark sizes, in the launch configuration that
+bench.py times: one fused launch over every batch of the 50M-point aerial scan
+(1M batches) and of the 300M-point clustered scan (1M-10M batches in shuffled
+order), each compared record for record with the oracle's closed form of the
+whole stream (Section 5: after every batch the octree depends only on the
+points so far, in arrival order).
+
+The oracle side needs about 25 GB of host memory and a minute or two of one
+core for the 300M-point case.
+"""
+import pytest
+
+import bench
+import oracle
+from helpers import assert_snapshots_equal
+from paper_2310_03567_gb300 import simlod
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.mark.parametrize("name", ["aerial", "clustered"])
+def test_full_size_fused_launch_matches_oracle(name):
+    w, root_log2 = bench.make_workload(name, None)
+    dev = simlod.points_tensor(w.points)
+    tree = bench.make_octree(w, root_log2)  # its stream waits for the copy above
+    ptrs = [dev.data_ptr() + int(o) * 16 for o in w.offsets]
+    assert tree.insert_many_ptrs(ptrs, [int(c) for c in w.counts]) == simlod.OK
+    assert tree.sync() == simlod.OK
+    st = tree.stats()
+    assert st["points"] == w.n_points and st["batches"] == len(w.counts)
+    snap = tree.snapshot()
+    tree.close()
+    del dev
+    ref = oracle.static_build(oracle.Config.make(root_min=w.root_min, root_log2=root_log2),
+                              w.stream())
+    assert_snapshots_equal(snap, ref)
+    assert int(snap.nodes["n_voxels"].sum()) == st["voxels"]
