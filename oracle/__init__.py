@@ -23,7 +23,7 @@ import numpy as np
 
 _DIR = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_DIR, "liboracle.so")
-_SOURCES = [os.path.join(_DIR, f) for f in ("incremental.c", "static.c")]
+_SOURCES = [os.path.join(_DIR, f) for f in ("incremental.c", "static.c", "render.c")]
 _HEADER = os.path.join(_DIR, "oracle.h")
 
 NODE_DTYPE = np.dtype([("level", "<u4"), ("is_inner", "<u4"), ("min", "<i4", (3,)),
@@ -82,7 +82,10 @@ def build(force: bool = False) -> str:
              any(os.path.getmtime(s) > os.path.getmtime(_LIB_PATH) for s in _SOURCES + [_HEADER]))
     if force or stale:
         tmp = _LIB_PATH + ".tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *_SOURCES, "-o", tmp]
+        # no contraction: the renderer's float arithmetic is one IEEE operation
+        # per written operator (so that the GPU can match it bit for bit)
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *_SOURCES,
+               "-o", tmp, "-lm"]
         proc = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
         if proc.returncode != 0:
             raise RuntimeError("oracle build failed:\n" + proc.stdout)
@@ -115,6 +118,8 @@ def _load():
         lib.orc_static_export.argtypes = [P, P, P, P]
         lib.orc_static_destroy.argtypes = [P]
         lib.orc_static_destroy.restype = None
+        lib.orc_render.argtypes = [ctypes.POINTER(Config), P, u64, P, P, P, ctypes.c_uint32,
+                                   ctypes.c_uint32, P, P, ctypes.POINTER(u64)]
         _lib = lib
     return _lib
 
@@ -216,3 +221,23 @@ def incremental_build(config: Config, batches) -> tuple[Snapshot, dict]:
         return o.snapshot(), o.stats()
     finally:
         o.close()
+
+
+def render(cfg: Config, snap: Snapshot, view_proj, width: int, height: int):
+    """Section 6 on the CPU: returns (framebuffer as uint64 [height, width],
+    per-node drawn flags in canonical order, number of drawn nodes).
+    view_proj: 16 float32, row-major; see render.c for the readings."""
+    lib = _load()
+    m = np.ascontiguousarray(np.asarray(view_proj, dtype=np.float32).reshape(16))
+    nodes = np.ascontiguousarray(snap.nodes)
+    points = np.ascontiguousarray(snap.points)
+    voxels = np.ascontiguousarray(snap.voxels)
+    fb = np.empty((height, width), np.uint64)
+    drawn = np.zeros(len(nodes), np.uint8)
+    nd = ctypes.c_uint64()
+    rc = lib.orc_render(ctypes.byref(cfg), nodes.ctypes.data, len(nodes), points.ctypes.data,
+                        voxels.ctypes.data, m.ctypes.data, width, height, fb.ctypes.data,
+                        drawn.ctypes.data, ctypes.byref(nd))
+    if rc != OK:
+        raise OracleError(rc, "orc_render")
+    return fb, drawn.astype(bool), int(nd.value)

@@ -6,7 +6,8 @@
  * call this code: the tests, the smoke check and the benchmark's CPU-baseline
  * leg are its only users. It shares no code with the CUDA library.
  *
- * Two independent implementations live here:
+ * Two independent implementations of the update live here (and render.c,
+ * the renderer of Section 6, for the frame-budget tests):
  *
  *  - incremental.c: a plain, sequential rendering of the paper's per-batch
  *    update (Section 5): expansion by repeated counting and splitting
@@ -114,6 +115,15 @@ void orc_static_sizes(const orc_static* t, orc_sizes* s);
 int orc_static_export(const orc_static* t, orc_node* nodes, orc_point_rec* points,
                       orc_voxel_rec* voxels);
 void orc_static_destroy(orc_static* t);
+
+/* render.c: Section 6, the level-of-detail selection and pixel-sized splats
+   of a canonical octree (see render.c for the readings). framebuffer holds
+   width * height entries ((float bits of depth) << 32 | rgba, all ones =
+   empty), drawn one flag per node. */
+int orc_render(const orc_config* cfg, const orc_node* nodes, uint64_t n_nodes,
+               const orc_point_rec* points, const orc_voxel_rec* voxels, const float view_proj[16],
+               uint32_t width, uint32_t height, uint64_t* framebuffer, uint8_t* drawn,
+               uint64_t* n_drawn);
 
 #ifdef __cplusplus
 }
