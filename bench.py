@@ -359,6 +359,29 @@ def run_ours(args):
     lat_f = [a.elapsed_time(b) for a, b in lat_fused]
     lat_p = [a.elapsed_time(b) for a, b in lat_plain]
 
+    # ---- one 1920x1080 frame of the whole octree (Section 6 renderer), from
+    # an oblique overview camera
+    side = float(1 << root_log2)
+    ctr = np.asarray(w.root_min, float) + side * np.array([0.5, 0.5, 0.02])
+    eye = ctr + side * np.array([-0.45, -0.55, 0.35])
+    cam = simlod.view_proj(eye, ctr, 60.0, 1920 / 1080)
+    frame = torch.empty((1080, 1920), dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        tree.render(cam, frame)
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(5):
+        tree.render(cam, frame)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    check(tree.sync(), "render")
+    rst = tree.stats()
+    render = {"ms": r0.elapsed_time(r1) / 5, "width": 1920, "height": 1080,
+              "nodes": rst["render_nodes"], "samples": rst["render_samples"],
+              "pixels_hit": int((frame != -1).sum().item())}
+    del frame
+
     # ---- end to end through the public API: pinned host stream -> HBM,
     # fused update, result (stats) back to the host, every step
     host_pts = torch.from_numpy(np.ascontiguousarray(w.points).view(np.uint8).reshape(-1, 16))
@@ -419,6 +442,7 @@ def run_ours(args):
         "update_counts": {"B": B, "S": S, "V": V, "K": K, "rounds": stats["rounds"],
                           "nodes": stats["nodes"]},
         "fused_phase_ms_per_step": phases,
+        "render_1080p": render,
         "gpu_launches": 2 * args.steps,
         "e2e": {"value": job_points / e2e_s / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": n_points * 16 + 16 * len(ptrs),

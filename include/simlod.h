@@ -116,6 +116,8 @@ typedef struct {
   uint64_t last_points, last_spilled, last_splits, last_voxels, last_iterations;
   int32_t sticky_status; /* the error that poisoned the handle, or 0 */
   uint32_t device_error_bits;
+  /* the last simlod_render: nodes drawn, points and voxels visited */
+  uint64_t render_nodes, render_samples;
 } simlod_stats;
 
 /* Per-kernel device time, accumulated while timing is enabled, and the
@@ -229,6 +231,28 @@ SIMLOD_API int simlod_get_stats(simlod_t* h, simlod_stats* out);
  * follow in node order sorted by cell. n_chunks is the length of the node's
  * chunk list, ceil(count / C) (Section 5.3). */
 SIMLOD_API int simlod_snapshot(simlod_t* h, simlod_snapshot_t* snap);
+
+/* Section 6: draw the octree into a caller-owned device framebuffer of
+ * width * height uint64_t entries (row-major, 8-byte aligned), each
+ * (float bits of depth) << 32 | rgba; all ones = empty. clear != 0 fills it
+ * with all ones first, else the octree is drawn over what is there (so
+ * several octrees can share a frame). Node selection: a node is drawn when
+ * its cube is in the view frustum, it is a leaf or at most 2^grid_log2
+ * pixels on screen, and its parent is larger than that (or it is the root);
+ * a drawn leaf splats its points, a drawn inner node its voxels, one pixel
+ * each; a pixel keeps the smallest word (the closest sample).
+ * view_proj: row-major 4x4, clip = M (x, y, z, 1) with the integer
+ * coordinates as float; depth = clip w; a sample is drawn when w > 0 and
+ * s = (clip.xy / w * 0.5 + 0.5) * (width, height) lies in [0,width)x[0,height)
+ * (pixel floor(s)). A cube is culled when its 8 corners are all outside one
+ * of x < -w, x > w, y < -w, y > w, w <= 0; its size on screen is the larger
+ * side of its corners' screen box (infinite with a corner at w <= 0). Float
+ * operations are single-precision IEEE, one per operator in that order, so
+ * the frame is reproducible bit for bit. Asynchronous on `stream`, ordered
+ * after the inserts enqueued before it on that stream; the octree is not
+ * changed. simlod_get_stats reports the nodes drawn and samples visited. */
+SIMLOD_API int simlod_render(simlod_t* h, const float view_proj[16], uint32_t width,
+                             uint32_t height, uint64_t* d_framebuffer, int clear, void* stream);
 
 /* Record CUDA events around every kernel launch (on the launching stream)
  * and accumulate per-kernel device time; enable = 0 stops, clear resets. */

@@ -114,13 +114,13 @@ struct Ctl {
   unsigned int alloc_seq;            // alloc_refs entries of this update
   unsigned int split_count;          // split-list entries of this update
   unsigned int ntasks;               // spill tasks (= freed chunks) of this update
-  unsigned int pad0;
+  unsigned int vis_count;            // nodes drawn by the last render
   unsigned long long st_batches, st_points, st_rejected, st_spilled, st_splits, st_voxels,
       st_iter_max, st_rounds;
   unsigned long long last_points, last_spilled, last_splits, last_voxels, last_iters;
   unsigned long long st_rejected_async;  // rejections inside fused launches
   unsigned int mv_count[2];              // entries of the two mover lists
-  unsigned long long pad1;
+  unsigned long long render_samples;     // points and voxels visited by the last render
   unsigned long long phase_ns[8];        // fused form: time per phase (see PH_*)
 };
 static_assert(sizeof(Ctl) % 16 == 0, "Ctl size");

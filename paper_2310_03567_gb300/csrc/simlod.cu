@@ -10,6 +10,7 @@
 
 #include "device.cuh"
 #include "fused.cuh"
+#include "render.cuh"
 #include "simlod.h"
 
 using namespace sl;
@@ -102,13 +103,13 @@ __global__ void k_end_rejected(Ctx c) { phase_end_rejected(c); }
 
 // ================================================================ host side
 
-enum KernelId { K_COUNT = 0, K_DECIDE, K_ADVANCE, K_STORE, K_END, K_FUSED, K_INIT, K_UNUSED };
+enum KernelId { K_COUNT = 0, K_DECIDE, K_ADVANCE, K_STORE, K_END, K_FUSED, K_INIT, K_RENDER };
 static const char* const kKernelNames[SIMLOD_N_KERNELS] = {
-    "count1", "decide", "advance", "store", "end", "fused_update", "init", "unused"};
+    "count1", "decide", "advance", "store", "end", "fused_update", "init", "render"};
 
 struct Layout {
   size_t ctl, fctl, batches, child, gridref, cnt, num, meta, pool, pending, alloc_refs, splits,
-      tasks, sp_cur, sp_rec, sp_gidx, b_cur, mv0, mv1, scur, hash, keys, staging, data, end;
+      tasks, sp_cur, sp_rec, sp_gidx, b_cur, mv0, mv1, scur, vis, hash, keys, staging, data, end;
   uint64_t hash_slots, max_chunks, max_splits, data_bytes;
 };
 
@@ -223,6 +224,7 @@ bool plan_layout(const simlod_config* c, size_t arena_bytes, Layout* L) {
   L->sp_rec = take(16 * S);
   L->sp_gidx = take(4 * S);
   L->scur = take(4 * N);
+  L->vis = take(4 * N);
   L->hash = take(sizeof(HSlot) * L->hash_slots);
   L->keys = take(sizeof(uint32_t) * c->backlog_capacity);
   L->staging = take(16 * B);
@@ -718,7 +720,40 @@ SIMLOD_API int simlod_get_stats(simlod_t* h, simlod_stats* out) {
   out->last_iterations = t.last_iters;
   out->sticky_status = h->sticky;
   out->device_error_bits = t.error;
+  out->render_nodes = t.vis_count;
+  out->render_samples = t.render_samples;
   return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_render(simlod_t* h, const float view_proj[16], uint32_t width,
+                             uint32_t height, uint64_t* d_framebuffer, int clear,
+                             void* cuda_stream) {
+  if (!h || !view_proj || !d_framebuffer || width == 0 || height == 0 ||
+      (reinterpret_cast<uintptr_t>(d_framebuffer) & 7u) ||
+      (uint64_t)width * height > (1ull << 32))
+    return SIMLOD_ERR_INVALID_ARG;
+  if (h->sticky) return SIMLOD_ERR_POISONED;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  h->last_stream = s;
+  View v;
+  for (int k = 0; k < 16; ++k) v.m[k] = view_proj[k];
+  v.W = (float)width;
+  v.H = (float)height;
+  v.lod = (float)(1u << h->cfg.grid_log2);
+  v.width = width;
+  v.height = height;
+  const Ctx& c = h->ctx;
+  uint32_t* vis = reinterpret_cast<uint32_t*>(h->arena + h->lay.vis);
+  unsigned long long* fb = reinterpret_cast<unsigned long long*>(d_framebuffer);
+  if (cudaMemsetAsync(&c.ctl->vis_count, 0, sizeof(unsigned int), s) != cudaSuccess ||
+      cudaMemsetAsync(&c.ctl->render_samples, 0, sizeof(unsigned long long), s) != cudaSuccess)
+    return SIMLOD_ERR_CUDA;
+  const unsigned grid = (unsigned)h->sm_count * 4;
+  return launch(h, K_RENDER, s, [&] {
+    if (clear) k_fb_clear<<<grid, BLOCK, 0, s>>>(fb, (uint64_t)width * height);
+    k_render_select<<<grid, BLOCK, 0, s>>>(c, v, vis);
+    k_render_draw<<<grid * 2, BLOCK, 0, s>>>(c, v, vis, fb);
+  });
 }
 
 SIMLOD_API int simlod_snapshot(simlod_t* h, simlod_snapshot_t* snap) {

@@ -69,7 +69,9 @@ class Stats(ctypes.Structure):
         "iterations_max", "rounds", "nodes", "chunks_bumped", "chunks_pool", "arena_bytes", "data_bytes",
         "data_used", "last_points", "last_spilled", "last_splits", "last_voxels",
         "last_iterations")] + [("sticky_status", ctypes.c_int32),
-                               ("device_error_bits", ctypes.c_uint32)]
+                               ("device_error_bits", ctypes.c_uint32),
+                               ("render_nodes", ctypes.c_uint64),
+                               ("render_samples", ctypes.c_uint64)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -116,6 +118,7 @@ SIGNATURES = {
     "simlod_status_string": (ctypes.c_char_p, [_I32]),
     "simlod_sample_node_noalloc": (_I32, [_P, _U64, ctypes.POINTER(ctypes.c_int32), _U32, _U32,
                                           _P, _U64, _P, _P]),
+    "simlod_render": (_I32, [_P, _P, _U32, _U32, _P, _I32, _P]),
 }
 
 
@@ -143,6 +146,31 @@ def status_string(status: int) -> str:
         return load().simlod_status_string(status).decode()
     except Exception:
         return f"status {status}"
+
+
+def view_proj(eye, target, fov_deg: float, aspect: float, up=(0.0, 0.0, 1.0)):
+    """Row-major 4x4 view-projection (16 float32) for simlod_render: a camera
+    at `eye` looking at `target` (coordinates in the octree's integer units),
+    vertical field of view fov_deg; depth = clip w = distance along the view
+    direction."""
+    import numpy as _np
+    eye, target = _np.asarray(eye, float), _np.asarray(target, float)
+    f = target - eye
+    f /= _np.linalg.norm(f)
+    u0 = _np.asarray(up, float)
+    if abs(float(f @ u0)) > 0.99:
+        u0 = _np.array([0.0, 1.0, 0.0])
+    s_ = _np.cross(f, u0)
+    s_ /= _np.linalg.norm(s_)
+    u = _np.cross(s_, f)
+    view = _np.eye(4)
+    view[0, :3], view[1, :3], view[2, :3] = s_, u, -f
+    view[:3, 3] = -view[:3, :3] @ eye
+    t = 1.0 / _np.tan(_np.radians(fov_deg) / 2)
+    proj = _np.zeros((4, 4))
+    proj[0, 0], proj[1, 1] = t / aspect, t
+    proj[2, 2], proj[2, 3], proj[3, 2] = -1.0, -1.0, -1.0
+    return (proj @ view).astype(_np.float32).reshape(16)
 
 
 def default_config(**overrides) -> Config:
@@ -331,6 +359,22 @@ class Octree:
         if rc != OK:
             raise SimlodError(rc, "simlod_get_timing")
         return {t.phase_name[k].decode(): float(t.phase_ms[k]) for k in range(N_PHASES)}
+
+    def render(self, view_proj, framebuffer, clear: bool = True, stream=None) -> None:
+        """Draw into framebuffer (a CUDA uint64/int64 tensor of [height, width])
+        with the row-major 4x4 view_proj (16 floats); see simlod_render."""
+        import numpy as _np
+        m = _np.ascontiguousarray(_np.asarray(view_proj, dtype=_np.float32).reshape(16))
+        if framebuffer.dim() != 2 or framebuffer.element_size() != 8 or not framebuffer.is_cuda \
+                or not framebuffer.is_contiguous():
+            raise ValueError("framebuffer must be a contiguous [height, width] 8-byte CUDA tensor")
+        height, width = framebuffer.shape
+        st = stream if stream is not None else self.stream
+        self._order(st, framebuffer)
+        rc = self._lib.simlod_render(self._h, m.ctypes.data, width, height,
+                                     framebuffer.data_ptr(), int(clear), _stream_ptr(st))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_render")
 
     def snapshot(self) -> Snapshot:
         s = Snapshot_t()
