@@ -415,6 +415,44 @@ def run_ours(args):
     achieved = upd_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms else 0.0
     ms_per_step = ms_total / args.steps
     value = job_points * args.steps / (ms_total * 1e-3) / 1e6
+    path = "fused persistent launch per step (every batch a full update)"
+
+    # ---- batched form (uneven batches): autotuned plan (merged updates, one
+    # persistent launch, replayed as a CUDA graph), timed like the fused form
+    batched = None
+    if args.workload == "mixed" or args.batched:
+        best, tune_ms = tree.autotune(ptrs, counts)
+        plan = tree.plan(ptrs, counts, merge_points=best.merge_points,
+                         blocks_per_sm=best.blocks_per_sm, use_graph=True)
+        params, graphed = plan.info()
+        for _ in range(args.warmup):
+            tree.reset()
+            check(plan.run(), "plan run")
+        check(tree.sync(), "batched warm-up")
+        bstats = tree.stats()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.steps):
+            tree.reset()
+            check(plan.run(), "plan run")
+        b1.record(stream)
+        torch.cuda.synchronize()
+        check(tree.sync(), "batched steps")
+        plan.close()
+        b_ms, b_points = aggregate(b0.elapsed_time(b1), n_points, dist, "cuda")
+        batched = {"value": b_points * args.steps / (b_ms * 1e-3) / 1e6, "unit": UNIT,
+                   "ms_per_step": b_ms / args.steps, "params": params, "graph": graphed,
+                   "updates_per_step": bstats["batches"], "autotune_best_ms": tune_ms,
+                   "vs_fused_unmerged": None, "vs_plain": None}
+        batched["vs_fused_unmerged"] = batched["value"] / value
+        path = ("batched form: autotuned plan (merged updates, one persistent launch, "
+                "CUDA graph) per step")
+        fused_unmerged = {"value": value, "ms_per_step": ms_per_step}
+        value, ms_per_step = batched["value"], batched["ms_per_step"]
     roofline_mpts = B / (upd_bytes / (peak * 1e9)) / 1e6
     tpp = TRAFFIC_PER_POINT.get(kernel_source_hash())
     traffic = tpp * B if tpp is not None else None
@@ -426,7 +464,7 @@ def run_ours(args):
         "config": {"workload": w.name, "batch_points": max_batch, "batches_per_step": len(ptrs),
                    "points_per_step": n_points, "leaf_capacity": cfg.leaf_capacity,
                    "chunk_points": cfg.chunk_points, "grid": 1 << cfg.grid_log2,
-                   "path": "fused persistent launch per step (every batch a full update)",
+                   "path": path,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (%.0f MB of points)" % (n_points * 16 / 2**20)},
         "latency_ms": {"fused_p50": percentile(lat_f, 50), "fused_p99": percentile(lat_f, 99),
@@ -443,12 +481,22 @@ def run_ours(args):
                           "nodes": stats["nodes"]},
         "fused_phase_ms_per_step": phases,
         "render_1080p": render,
+        "batched": batched,
         "gpu_launches": 2 * args.steps,
         "e2e": {"value": job_points / e2e_s / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": n_points * 16 + 16 * len(ptrs),
                 "d2h_bytes_per_step": CTL_BYTES},
         "clocks": clk,
     }
+    if batched is not None:
+        batched["vs_plain"] = batched["value"] / line["plain"]["value"]
+        line["fused_unmerged"] = fused_unmerged
+        # merged updates re-insert fewer stored points: their own bytes per point
+        b_alg = update_alg_bytes(B, bstats["spilled"], V, K, grid_bytes)
+        b_roof = B / (b_alg / (peak * 1e9)) / 1e6
+        line["update_roofline"] = {"alg_bytes_per_point": b_alg / B, "roofline_mpts": b_roof,
+                                   "frac": value / world / b_roof, "form": "batched"}
+        line["update_counts"]["S_batched"] = bstats["spilled"]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline((w, root_log2), args.cpu_budget)
     if rank == 0:
@@ -471,6 +519,8 @@ def main():
     ap.add_argument("--ref-batches", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", action="store_true",
+                    help="also time the batched form (always on for --workload mixed)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -205,6 +205,47 @@ SIMLOD_API int simlod_insert_batch_host(simlod_t* h, const simlod_point* h_pts, 
 SIMLOD_API int simlod_insert_batches(simlod_t* h, const simlod_point* const* d_batches,
                                      const uint64_t* counts, uint32_t n_batches, void* stream);
 
+/* Batched form: a plan for a fixed list of uneven batches (device pointers,
+ * 16-byte aligned, at most 16,384), run as one CUDA graph (when capture is
+ * possible, else as direct launches) of three kernels: a check of every batch
+ * against the root cube (a batch with a point outside it is rejected whole,
+ * without change, as simlod_insert_batch would; simlod_sync then returns
+ * SIMLOD_ERR_OUT_OF_BOUNDS once), a grouping of the valid batches, in order,
+ * into updates of up to merge_points points, and one persistent launch that
+ * applies the updates (a merged update is first gathered into the handle's
+ * staging buffer). Merging consecutive batches leaves the octree unchanged:
+ * after any prefix of the stream it does not depend on how the stream was cut
+ * into batches (Section 5); gidx follows the order of the list. The plan
+ * keeps the pointers: a caller refills the same buffers and runs the plan
+ * again. simlod_plan_create allocates a small device table (about 80 bytes per
+ * batch, cudaMalloc) that simlod_plan_destroy frees; it waits for the plan's
+ * last run. One handle runs one plan or fused launch at a time (stream
+ * order). */
+typedef struct simlod_plan simlod_plan_t;
+typedef struct {
+  uint64_t merge_points;  /* merged update size; 0 = one update per batch; at most max_batch_points */
+  uint32_t blocks_per_sm; /* persistent blocks (512 threads) per SM: 1, 2, or 0 = as many as fit */
+  uint32_t use_graph;     /* capture the run in a CUDA graph */
+  uint32_t reserved;
+} simlod_plan_params;
+SIMLOD_API int simlod_plan_create(simlod_t* h, const simlod_point* const* d_batches,
+                                  const uint64_t* counts, uint32_t n_batches,
+                                  const simlod_plan_params* params, simlod_plan_t** out);
+/* Enqueue one run of the plan on `stream` (asynchronous; errors at simlod_sync). */
+SIMLOD_API int simlod_plan_run(simlod_plan_t* plan, void* stream);
+/* The parameters in effect (merge_points clamped) and whether runs replay a graph. */
+SIMLOD_API int simlod_plan_info(const simlod_plan_t* plan, simlod_plan_params* params,
+                                uint32_t* graphed);
+SIMLOD_API int simlod_plan_destroy(simlod_plan_t* plan);
+/* Autotuner of the batched form: times plans for this batch list over merge
+ * sizes (none, 256k, 1M, 2M, 4M, 8M points, max_batch_points; those below
+ * max_batch_points) and 1 or 2 blocks per SM, on `h` itself (reset before
+ * every trial and at the end: pass a scratch handle of the same configuration
+ * to keep an octree), and returns the fastest parameters and their time. */
+SIMLOD_API int simlod_plan_autotune(simlod_t* h, const simlod_point* const* d_batches,
+                                    const uint64_t* counts, uint32_t n_batches, void* stream,
+                                    simlod_plan_params* best, double* best_ms);
+
 /* Frame-budget update (Section 7.2): as simlod_insert_batches, but before
  * starting batch k > 0 the kernel checks the time since the launch began
  * (the GPU's global timer); once it exceeds budget_ns it stops. Batches are

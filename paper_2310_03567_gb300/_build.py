@@ -55,8 +55,9 @@ def library_command(out: str = LIB_PATH, extra: list[str] | None = None) -> list
     # -dlcm=cg: plain global loads are served by the coherent L2, not the
     # per-SM L1, because the persistent kernel re-reads node tables, split
     # lists and grids that other blocks rewrote after a grid barrier (L1s are
-    # not coherent with each other within one grid). Read-only inputs use
-    # __ldg and keep the L1/texture path.
+    # not coherent with each other within one grid). Batch points are read
+    # with __ldcg too: a merged update reads them from a staging buffer that
+    # the same launch has just written.
     return ([_nvcc(), *ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17", "-shared",
              "-Xptxas", "-dlcm=cg",
              "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -604,7 +604,7 @@ __device__ void phase_count1(const Ctx& c, uint32_t* smem, uint32_t n_nodes, con
   for (uint64_t w = warp0; w * 32 < n; w += nwarps) {
     uint64_t i = w * 32 + lane;
     bool valid = i < n;
-    int4 p = valid ? __ldg(pts + i) : make_int4(0, 0, 0, 0);
+    int4 p = valid ? __ldcg(pts + i) : make_int4(0, 0, 0, 0);
     uint32_t rx = 0, ry = 0, rz = 0;
     if (valid && !rel_coords(c, p, rx, ry, rz)) {
       atomicOr(&c.ctl->reject, 1u);
@@ -808,7 +808,7 @@ __device__ void phase_advance(const Ctx& c, uint32_t* smem, uint32_t n_nodes, co
           p = c.sp_rec[idx];
           g = c.sp_gidx[idx];
         } else {
-          p = __ldg(pts + idx);
+          p = __ldcg(pts + idx);
           g = (uint32_t)(base + idx);
         }
       }
@@ -1130,7 +1130,7 @@ __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned 
       const uint64_t i = b0 + j * wstride + lane;
       valid[j] = i < n;
       node[j] = valid[j] ? c.b_cur[i] : 0u;
-      p[j] = valid[j] ? __ldg(pts + i) : make_int4(0, 0, 0, 0);
+      p[j] = valid[j] ? __ldcg(pts + i) : make_int4(0, 0, 0, 0);
       if (valid[j] && node[j] >= c.max_nodes) {
         set_error(c, E_INTERNAL);
         valid[j] = false;

@@ -20,9 +20,19 @@ constexpr int FUSED_BLOCK = PHASE_BLOCK;
 constexpr unsigned long long NO_BUDGET = ~0ull;
 constexpr uint32_t MAX_FUSED_BATCHES = 16384;
 
+// One update of the fused launch: n points at pts, or, with nseg > 0, the
+// segments [seg0, seg0 + nseg) of the segment table, gathered into the
+// staging buffer first (a merged update of several batches).
 struct BatchDesc {
   const int4* pts;
   unsigned long long n;
+  uint32_t seg0, nseg;
+};
+
+// A batch inside a merged update: n points at src go to staging[dst, dst + n).
+struct PlanSeg {
+  const int4* src;
+  uint32_t n, dst;
 };
 
 // Per-launch control words of the fused kernel (arena).
@@ -101,24 +111,45 @@ struct PhaseClock {
 // batch other than the first, stop once more than budget_ns has passed since
 // the launch began (Section 7.2's frame budget; batches are never cut);
 // NO_BUDGET disables the check.
+//
+// n_dev != nullptr: the number of updates is read from the device (written by
+// the planning kernel before this launch) instead of n_batches.
 __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, const BatchDesc* batches,
                                                         uint32_t n_batches, FusedCtl* f,
                                                         unsigned long long budget_ns,
-                                                        uint32_t max_iters) {
+                                                        uint32_t max_iters,
+                                                        const unsigned int* n_dev,
+                                                        const PlanSeg* segs) {
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t warp0 = tid / 32, nwarps = nthreads / 32;
   const unsigned long long t_begin = globaltimer_ns();
   extern __shared__ uint32_t smem[];  // node-table cache (PHASE_SMEM_BYTES)
   PhaseClock clk{t_begin};
-  for (uint32_t b = 0; b < n_batches; ++b) {
+  const uint32_t nb = n_dev ? min(vload(n_dev), n_batches) : n_batches;
+  for (uint32_t b = 0; b < nb; ++b) {
     // every value read here was written before the last barrier and is not
     // written again before the next one, so all threads decide alike
     if (vload(&f->stop)) return;
-    const BatchDesc bd = batches[b];
+    BatchDesc bd = batches[b];
     const unsigned long long base = vload(&c.ctl->base);
     const uint32_t nodes0 = vload(&c.ctl->n_nodes);
     bool rejected = false;
+    if (bd.nseg && bd.n) {
+      // merged update: gather its batches into the staging buffer
+      if (bd.n > c.max_batch) {
+        if (tid == 0) set_error(c, E_INTERNAL);
+        return;
+      }
+      for (uint32_t k = 0; k < bd.nseg; ++k) {
+        const PlanSeg sg = segs[bd.seg0 + k];
+        if ((unsigned long long)sg.dst + sg.n > bd.n) continue;
+        for (uint64_t i = tid; i < sg.n; i += nthreads) c.staging[sg.dst + i] = __ldg(sg.src + i);
+      }
+      if (!grid_barrier(c, f)) return;
+      clk.tick(c, PH_OTHER);
+      bd.pts = c.staging;
+    }
     if (bd.n) {
       phase_count1(c, smem, nodes0, bd.pts, bd.n, base, warp0, nwarps);
       if (!grid_barrier(c, f)) return;
@@ -182,6 +213,83 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
   }
   if (blockIdx.x == 0 && threadIdx.x == 0)
     atomicAdd(&c.ctl->phase_ns[PH_LAUNCH], globaltimer_ns() - t_begin);
+}
+
+// ------------------------------------------------------------ batched form
+//
+// Planning of a list of uneven batches on the device, before the fused
+// launch: every batch is checked against the root cube (a batch with a point
+// outside it is rejected whole, as simlod_insert_batch would), then the valid
+// batches are merged, in order, into updates of up to `merge` points. Merging
+// consecutive batches gives the octree they would give one by one (the
+// octree after a prefix of the stream does not depend on how it was cut into
+// batches; Section 5), with fewer expansion rounds and grid barriers.
+
+struct PlanInput {
+  const int4* pts;
+  unsigned long long n;
+};
+
+// Units of 4,096 points over all batches; tile0[k] = first unit of batch k
+// (n_in + 1 entries). Sets bad[k] when batch k has a point outside the cube.
+__global__ void k_plan_validate(Ctx c, const PlanInput* in, const uint32_t* tile0, uint32_t n_in,
+                                unsigned int* bad) {
+  const uint32_t units = tile0[n_in];
+  for (uint32_t u = blockIdx.x; u < units; u += gridDim.x) {
+    uint32_t lo = 0, hi = n_in;  // batch k with tile0[k] <= u < tile0[k + 1]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) / 2;
+      if (tile0[mid] <= u) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t k = lo;
+    const PlanInput b = in[k];
+    const uint64_t first = (uint64_t)(u - tile0[k]) * 4096;
+    bool out = false;
+    for (uint64_t i = first + threadIdx.x; i < b.n && i < first + 4096; i += blockDim.x) {
+      uint32_t rx, ry, rz;
+      out |= !rel_coords(c, __ldg(b.pts + i), rx, ry, rz);
+    }
+    if (__syncthreads_or(out) && threadIdx.x == 0) bad[k] = 1u;
+  }
+}
+
+// One thread: group the valid batches into updates, count the rejected ones.
+__global__ void k_plan_groups(Ctx c, const PlanInput* in, uint32_t n_in, const unsigned int* bad,
+                              unsigned long long merge, BatchDesc* groups, PlanSeg* segs,
+                              unsigned int* n_groups) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  uint32_t ng = 0, ns = 0, rejected = 0;
+  BatchDesc g{nullptr, 0, 0, 0};
+  auto close = [&]() {
+    if (g.n == 0) return;
+    if (g.nseg == 1) {  // a single batch is read in place
+      g.pts = segs[g.seg0].src;
+      g.nseg = 0;
+    }
+    groups[ng++] = g;
+    g = BatchDesc{nullptr, 0, ns, 0};
+  };
+  g.seg0 = 0;
+  for (uint32_t k = 0; k < n_in; ++k) {
+    if (bad[k]) {
+      ++rejected;
+      continue;
+    }
+    const unsigned long long n = in[k].n;
+    if (n == 0) continue;
+    if (g.n && g.n + n > merge) close();
+    if (g.nseg == 0) g.seg0 = ns;
+    segs[ns++] = PlanSeg{in[k].pts, (uint32_t)n, (uint32_t)g.n};
+    g.n += n;
+    ++g.nseg;
+  }
+  close();
+  *n_groups = ng;
+  if (rejected) {
+    c.ctl->st_rejected += rejected;
+    c.ctl->st_rejected_async += rejected;
+  }
 }
 
 }  // namespace sl

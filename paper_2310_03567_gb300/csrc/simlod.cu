@@ -477,7 +477,7 @@ int launch_fused(simlod_t* h, const simlod_point* const* d_batches, const uint64
   // the staging table may still feed the previous copy
   if (cudaEventSynchronize(h->desc_done) != cudaSuccess) return poison(h, SIMLOD_ERR_CUDA);
   for (uint32_t k = 0; k < n; ++k)
-    h->desc_host[k] = BatchDesc{reinterpret_cast<const int4*>(d_batches[k]), counts[k]};
+    h->desc_host[k] = BatchDesc{reinterpret_cast<const int4*>(d_batches[k]), counts[k], 0, 0};
   h->last_stream = s;
   if (cudaMemcpyAsync(h->batches_dev, h->desc_host, sizeof(BatchDesc) * n,
                       cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -488,7 +488,9 @@ int launch_fused(simlod_t* h, const simlod_point* const* d_batches, const uint64
   const BatchDesc* bt = h->batches_dev;
   FusedCtl* f = h->fctl_dev;
   uint32_t max_iters = h->cfg.max_expand_iters ? h->cfg.max_expand_iters : h->cfg.root_log2 + 1;
-  void* args[] = {&c, &bt, &n, &f, &budget_ns, &max_iters};
+  const unsigned int* n_dev = nullptr;
+  const PlanSeg* segs = nullptr;
+  void* args[] = {&c, &bt, &n, &f, &budget_ns, &max_iters, &n_dev, &segs};
   cudaError_t le = cudaSuccess;
   int rc = launch(h, K_FUSED, s, [&] {
     le = cudaLaunchCooperativeKernel((const void*)k_fused, dim3(h->fused_grid),
@@ -676,6 +678,225 @@ SIMLOD_API int simlod_frame_update(simlod_t* h, const simlod_point* const* d_bat
   int rc = launch_fused(h, d_batches, counts, n_batches, budget, static_cast<cudaStream_t>(stream));
   if (rc) return rc;
   return finish_fused(h, consumed);
+}
+
+// ------------------------------------------------------------ batched form
+
+struct simlod_plan {
+  simlod_t* h;
+  simlod_plan_params p;
+  uint32_t n;           // input batches
+  uint64_t total;       // their points
+  uint32_t units;       // 4,096-point validation units
+  unsigned grid;        // blocks of the persistent launch
+  void* dmem;           // the plan's device tables (one cudaMalloc)
+  PlanInput* in;
+  uint32_t* tile0;
+  unsigned int* bad;
+  BatchDesc* groups;
+  PlanSeg* segs;
+  unsigned int* n_groups;
+  cudaStream_t cap;     // capture stream
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  bool graphed;
+  cudaStream_t last;    // stream of the last run
+};
+
+namespace {
+
+// The launch sequence of one run: validate, group, fused update.
+int plan_enqueue(simlod_plan_t* P, cudaStream_t s) {
+  simlod_t* h = P->h;
+  Ctx c = h->ctx;
+  if (cudaMemsetAsync(P->bad, 0, 4ull * P->n, s) != cudaSuccess ||
+      cudaMemsetAsync(P->n_groups, 0, sizeof(unsigned int), s) != cudaSuccess)
+    return SIMLOD_ERR_CUDA;
+  const unsigned vg = std::max(1u, std::min<unsigned>(P->units, (unsigned)h->sm_count * 8));
+  k_plan_validate<<<vg, BLOCK, 0, s>>>(c, P->in, P->tile0, P->n, P->bad);
+  k_plan_groups<<<1, 1, 0, s>>>(c, P->in, P->n, P->bad, P->p.merge_points, P->groups, P->segs,
+                                P->n_groups);
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemsetAsync(h->fctl_dev, 0, sizeof(FusedCtl), s) != cudaSuccess)
+    return SIMLOD_ERR_CUDA;
+  const BatchDesc* bt = P->groups;
+  uint32_t n = P->n;
+  FusedCtl* f = h->fctl_dev;
+  unsigned long long budget = NO_BUDGET;
+  uint32_t max_iters = h->cfg.max_expand_iters ? h->cfg.max_expand_iters : h->cfg.root_log2 + 1;
+  const unsigned int* n_dev = P->n_groups;
+  const PlanSeg* segs = P->segs;
+  void* args[] = {&c, &bt, &n, &f, &budget, &max_iters, &n_dev, &segs};
+  if (cudaLaunchCooperativeKernel((const void*)k_fused, dim3(P->grid), dim3(FUSED_BLOCK), args,
+                                  PHASE_SMEM_BYTES, s) != cudaSuccess)
+    return SIMLOD_ERR_CUDA;
+  return SIMLOD_OK;
+}
+
+}  // namespace
+
+SIMLOD_API int simlod_plan_create(simlod_t* h, const simlod_point* const* d_batches,
+                                  const uint64_t* counts, uint32_t n_batches,
+                                  const simlod_plan_params* params, simlod_plan_t** out) {
+  if (!h || !out || !params || (n_batches && (!d_batches || !counts)) ||
+      n_batches > MAX_FUSED_BATCHES || params->blocks_per_sm > 2)
+    return SIMLOD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (h->sticky) return SIMLOD_ERR_POISONED;
+  if (h->fused_grid < 1) return SIMLOD_ERR_CUDA;
+  uint64_t total = 0;
+  std::vector<PlanInput> in(n_batches);
+  std::vector<uint32_t> tile0(n_batches + 1, 0);
+  for (uint32_t k = 0; k < n_batches; ++k) {
+    if (counts[k] > h->cfg.max_batch_points) return SIMLOD_ERR_INVALID_ARG;
+    if (counts[k] && (!d_batches[k] || (reinterpret_cast<uintptr_t>(d_batches[k]) & 15u)))
+      return SIMLOD_ERR_INVALID_ARG;
+    in[k] = PlanInput{reinterpret_cast<const int4*>(d_batches[k]), counts[k]};
+    total += counts[k];
+    tile0[k + 1] = tile0[k] + (uint32_t)((counts[k] + 4095) / 4096);
+  }
+  auto* P = new simlod_plan();
+  P->h = h;
+  P->p = *params;
+  P->p.merge_points = std::min<uint64_t>(params->merge_points, h->cfg.max_batch_points);
+  P->n = n_batches;
+  P->total = total;
+  P->units = tile0[n_batches];
+  const unsigned per_sm = (unsigned)h->fused_grid / (unsigned)h->sm_count;
+  P->grid = (unsigned)h->sm_count *
+            (params->blocks_per_sm ? std::min<unsigned>(params->blocks_per_sm, per_sm) : per_sm);
+  P->last = h->last_stream;
+  const size_t nb = std::max<uint32_t>(n_batches, 1);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = align_up(o, 256);
+    o = at + bytes;
+    return at;
+  };
+  const size_t o_in = take(sizeof(PlanInput) * nb), o_t0 = take(4 * (nb + 1)),
+               o_bad = take(4 * nb), o_g = take(sizeof(BatchDesc) * nb),
+               o_s = take(sizeof(PlanSeg) * nb), o_ng = take(16);
+  if (cudaMalloc(&P->dmem, o) != cudaSuccess) {
+    delete P;
+    return SIMLOD_ERR_CUDA;
+  }
+  uint8_t* d = static_cast<uint8_t*>(P->dmem);
+  P->in = reinterpret_cast<PlanInput*>(d + o_in);
+  P->tile0 = reinterpret_cast<uint32_t*>(d + o_t0);
+  P->bad = reinterpret_cast<unsigned int*>(d + o_bad);
+  P->groups = reinterpret_cast<BatchDesc*>(d + o_g);
+  P->segs = reinterpret_cast<PlanSeg*>(d + o_s);
+  P->n_groups = reinterpret_cast<unsigned int*>(d + o_ng);
+  if ((n_batches && cudaMemcpy(P->in, in.data(), sizeof(PlanInput) * n_batches,
+                               cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(P->tile0, tile0.data(), 4ull * (n_batches + 1), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    cudaFree(P->dmem);
+    delete P;
+    return SIMLOD_ERR_CUDA;
+  }
+  if (params->use_graph && n_batches) {
+    // capture the launch sequence once; replays skip the per-launch host work
+    bool ok = cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const int rc = plan_enqueue(P, P->cap);
+      const bool ended = cudaStreamEndCapture(P->cap, &P->graph) == cudaSuccess;
+      ok = rc == SIMLOD_OK && ended && P->graph &&
+           cudaGraphInstantiate(&P->exec, P->graph, 0) == cudaSuccess;
+    }
+    cudaGetLastError();  // a failed capture leaves no error behind: runs launch directly
+    P->graphed = ok;
+  }
+  *out = P;
+  return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_plan_run(simlod_plan_t* P, void* stream) {
+  if (!P) return SIMLOD_ERR_INVALID_ARG;
+  simlod_t* h = P->h;
+  if (h->sticky) return SIMLOD_ERR_POISONED;
+  if (P->n == 0) return SIMLOD_OK;
+  if (h->base + P->total > (1ull << 32)) return SIMLOD_ERR_TOO_MANY_POINTS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->last_stream = s;
+  P->last = s;
+  int rc = SIMLOD_OK;
+  const int lr = launch(h, K_FUSED, s, [&] {
+    if (P->graphed) {
+      if (cudaGraphLaunch(P->exec, s) != cudaSuccess) rc = SIMLOD_ERR_CUDA;
+    } else {
+      rc = plan_enqueue(P, s);
+    }
+  });
+  if (rc || lr) return poison(h, SIMLOD_ERR_CUDA);
+  h->base += P->total;  // upper bound until the next control-block read
+  h->mirror_stale = true;
+  return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_plan_info(const simlod_plan_t* P, simlod_plan_params* params,
+                                uint32_t* graphed) {
+  if (!P) return SIMLOD_ERR_INVALID_ARG;
+  if (params) *params = P->p;
+  if (graphed) *graphed = P->graphed ? 1u : 0u;
+  return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_plan_destroy(simlod_plan_t* P) {
+  if (!P) return SIMLOD_ERR_INVALID_ARG;
+  cudaStreamSynchronize(P->last);
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  if (P->cap) cudaStreamDestroy(P->cap);
+  if (P->dmem) cudaFree(P->dmem);
+  delete P;
+  return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_plan_autotune(simlod_t* h, const simlod_point* const* d_batches,
+                                    const uint64_t* counts, uint32_t n_batches, void* stream,
+                                    simlod_plan_params* best, double* best_ms) {
+  if (!h || !best || (n_batches && (!d_batches || !counts))) return SIMLOD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint64_t mb = h->cfg.max_batch_points;
+  std::vector<uint64_t> merges = {0};
+  for (uint64_t m : {1ull << 18, 1ull << 20, 1ull << 21, 1ull << 22, 1ull << 23})
+    if (m < mb) merges.push_back(m);
+  merges.push_back(mb);
+  const unsigned per_sm = (unsigned)h->fused_grid / std::max(1, h->sm_count);
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+    return SIMLOD_ERR_CUDA;
+  double best_t = -1.0;
+  for (unsigned bps = 1; bps <= std::max(1u, std::min(per_sm, 2u)); ++bps) {
+    for (uint64_t m : merges) {
+      simlod_plan_params p{m, bps, 1, 0};
+      simlod_plan_t* P = nullptr;
+      if (simlod_reset(h, s) != SIMLOD_OK) continue;
+      if (simlod_plan_create(h, d_batches, counts, n_batches, &p, &P) != SIMLOD_OK) continue;
+      auto ran = [&] {  // rejected batches are fine; device errors are not
+        const int r = simlod_sync(h);
+        return r == SIMLOD_OK || r == SIMLOD_ERR_OUT_OF_BOUNDS;
+      };
+      float ms = -1.0f;
+      if (simlod_plan_run(P, s) == SIMLOD_OK && ran() && simlod_reset(h, s) == SIMLOD_OK &&
+          cudaEventRecord(a, s) == cudaSuccess && simlod_plan_run(P, s) == SIMLOD_OK &&
+          cudaEventRecord(b, s) == cudaSuccess && ran())
+        cudaEventElapsedTime(&ms, a, b);
+      simlod_plan_destroy(P);
+      if (ms >= 0.0f && (best_t < 0.0 || ms < best_t)) {
+        best_t = ms;
+        *best = p;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  const int rr = simlod_reset(h, s);
+  if (best_t < 0.0) return SIMLOD_ERR_CUDA;
+  if (best_ms) *best_ms = best_t;
+  return rr;
 }
 
 SIMLOD_API int simlod_reset(simlod_t* h, void* stream) {

@@ -119,7 +119,21 @@ SIGNATURES = {
     "simlod_sample_node_noalloc": (_I32, [_P, _U64, ctypes.POINTER(ctypes.c_int32), _U32, _U32,
                                           _P, _U64, _P, _P]),
     "simlod_render": (_I32, [_P, _P, _U32, _U32, _P, _I32, _P]),
+    "simlod_plan_create": (_I32, [_P, _P, _P, _U32, _P, ctypes.POINTER(_P)]),
+    "simlod_plan_run": (_I32, [_P, _P]),
+    "simlod_plan_info": (_I32, [_P, _P, ctypes.POINTER(_U32)]),
+    "simlod_plan_destroy": (_I32, [_P]),
+    "simlod_plan_autotune": (_I32, [_P, _P, _P, _U32, _P, _P, ctypes.POINTER(ctypes.c_double)]),
 }
+
+
+class PlanParams(ctypes.Structure):
+    _fields_ = [("merge_points", ctypes.c_uint64), ("blocks_per_sm", ctypes.c_uint32),
+                ("use_graph", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {"merge_points": int(self.merge_points), "blocks_per_sm": int(self.blocks_per_sm),
+                "use_graph": int(self.use_graph)}
 
 
 def load(path: str | None = None):
@@ -376,6 +390,27 @@ class Octree:
         if rc != OK:
             raise SimlodError(rc, "simlod_render")
 
+    def plan(self, ptrs, counts, merge_points: int = 0, blocks_per_sm: int = 0,
+             use_graph: bool = True) -> "Plan":
+        """Batched form over raw 16-byte-aligned device pointers (kept by the
+        plan; the caller keeps the buffers alive and orders their writes)."""
+        return Plan(self, ptrs, counts, PlanParams(merge_points, blocks_per_sm, int(use_graph), 0))
+
+    def autotune(self, ptrs, counts, stream=None):
+        """Fastest batched-form parameters for this batch list (resets the
+        octree); returns (PlanParams, ms)."""
+        n = len(ptrs)
+        p = (ctypes.c_void_p * max(n, 1))(*ptrs)
+        c = (ctypes.c_uint64 * max(n, 1))(*counts)
+        best = PlanParams()
+        ms = ctypes.c_double()
+        st = stream if stream is not None else self.stream
+        rc = self._lib.simlod_plan_autotune(self._h, p, c, n, _stream_ptr(st), ctypes.byref(best),
+                                            ctypes.byref(ms))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_plan_autotune")
+        return best, float(ms.value)
+
     def snapshot(self) -> Snapshot:
         s = Snapshot_t()
         rc = self._lib.simlod_snapshot(self._h, ctypes.byref(s))
@@ -415,3 +450,41 @@ def make_arena(cfg: Config, data_bytes: int, device="cuda"):
     """Allocate a uint8 CUDA tensor large enough for cfg and data_bytes."""
     import torch
     return torch.empty(arena_bytes(cfg, data_bytes), dtype=torch.uint8, device=device)
+
+
+class Plan:
+    """A batched-form plan bound to an Octree (see simlod_plan_create)."""
+
+    def __init__(self, tree: "Octree", ptrs, counts, params: PlanParams):
+        self.tree = tree
+        n = len(ptrs)
+        p = (ctypes.c_void_p * max(n, 1))(*ptrs)
+        c = (ctypes.c_uint64 * max(n, 1))(*counts)
+        h = ctypes.c_void_p()
+        rc = tree._lib.simlod_plan_create(tree._h, p, c, n, ctypes.byref(params), ctypes.byref(h))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_plan_create")
+        self._h = h
+
+    def run(self, stream=None) -> int:
+        st = stream if stream is not None else self.tree.stream
+        return self.tree._lib.simlod_plan_run(self._h, _stream_ptr(st))
+
+    def info(self):
+        p = PlanParams()
+        g = ctypes.c_uint32()
+        rc = self.tree._lib.simlod_plan_info(self._h, ctypes.byref(p), ctypes.byref(g))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_plan_info")
+        return p.as_dict(), bool(g.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.tree._lib.simlod_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
