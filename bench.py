@@ -164,7 +164,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    workload = make_workload(args.workload, args.points)
+    # the serving trace's octrees are terrain / uniform / clustered streams;
+    # the oracle is timed on the terrain (aerial) stream for it
+    workload = make_workload("aerial" if args.workload == "serving" else args.workload,
+                             args.points)
     w, root_log2 = workload
     import oracle
     cfg = oracle.Config.make(root_min=w.root_min, root_log2=root_log2)
@@ -507,6 +510,123 @@ def run_ours(args):
     return 0
 
 
+def serving_setup(scale: float, seed: int = 4):
+    """The serving configuration: 16 octrees (sizes log-uniform in
+    [5M, 200M] points times `scale`; uniform / terrain / clustered in turn),
+    each with its own stream, arena and overview camera."""
+    import torch
+
+    from paper_2310_03567_gb300 import serving, simlod, synth
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(5e6), np.log(2e8), 16)) * scale
+    streams, specs = [], []
+    for k, n in enumerate(int(max(1000, s)) for s in sizes):
+        kind = ("uniform", "terrain", "clustered")[k % 3]
+        if kind == "uniform":
+            pts, root = synth.uniform(seed * 100 + k, 1 << 20, n), 20
+        elif kind == "terrain":
+            pts, root = synth.terrain(seed * 100 + k, n), 22
+        else:
+            quads = max(50, int(20_000 * n / 300e6))
+            pts, root = synth.clustered(seed * 100 + k, quads, n), 21
+        side = float(1 << root)
+        ctr = side * np.array([0.5, 0.5, 0.05])
+        cam = simlod.view_proj(ctr + side * np.array([-0.45, -0.55, 0.35]), ctr, 60.0, 16 / 9)
+        # a uniform octree can split a whole level at once: every stored
+        # point may be re-inserted in one update, and each may make a voxel
+        cap = min(max(16 << 20, n + 5_000_000), (1 << 31) - 1)
+        cfg = simlod.default_config(root_log2=root, max_batch_points=5_000_000,
+                                    spill_capacity=cap, backlog_capacity=cap, max_nodes=1 << 20)
+        specs.append(serving.OctreeSpec(cfg, max(256 << 20, n * 80), cam))
+        host = torch.from_numpy(pts.view(np.uint8).reshape(-1, 16)).pin_memory()
+        streams.append(host)
+    return streams, specs
+
+
+def run_serving(args):
+    """Serving form: requests (log-uniform 100k-5M points) arrive by a Poisson
+    process at ~70 % of the plain path's measured capacity; the same trace is
+    served by the serving form and by a plain server (one request per update,
+    one update at a time)."""
+    import torch
+
+    from paper_2310_03567_gb300 import serving, simlod
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    rank = int(os.environ.get("RANK", "0"))
+    simlod.load()
+    streams, specs = serving_setup(args.serving_scale, seed=4 + rank)
+    total = sum(int(s.shape[0]) for s in streams)
+    # capacity of the plain path on this box: one octree, 1M-point requests
+    k0 = max(range(len(streams)), key=lambda k: streams[k].shape[0])
+    cal = serving.Server([specs[k0]], hbm_budget=1 << 40, plain=True)
+    n_cal = min(int(streams[k0].shape[0]), 20_000_000)
+    cal_reqs = [serving.Request(0, streams[k0][o:o + 1_000_000], 0.0)
+                for o in range(0, n_cal, 1_000_000)]
+    cal.run(cal_reqs)
+    cap = cal.report()["mpts_per_s"] * 1e6
+    cal.close()
+    rate = 0.7 * cap
+    reqs = serving.poisson_requests(streams, 100_000, 5_000_000, rate, seed=7)
+    arenas = sum(simlod.arena_bytes(sp.cfg, sp.data_bytes) for sp in specs)
+    budget = arenas + (4 << 30)
+    out = {}
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    for name, plain in (("serving", False), ("plain", True)):
+        for r in reqs:
+            r.admitted = r.done = -1.0
+        srv = serving.Server(specs, hbm_budget=budget, compute_slots=2, frame_ms=33.3,
+                             plain=plain)
+        if not plain:
+            clocks.start()
+        srv.run(reqs)
+        if not plain:
+            clk = clocks.stop()
+        out[name] = srv.report()
+        srv.close()
+        torch.cuda.empty_cache()
+    # saturated: the whole trace queued at once (throughput at capacity)
+    sat = {}
+    for name, plain in (("serving", False), ("plain", True)):
+        for r in reqs:
+            r.admitted = r.done = -1.0
+            r.arrival = 0.0
+        srv = serving.Server(specs, hbm_budget=budget, compute_slots=2, frame_ms=33.3,
+                             plain=plain)
+        srv.run(reqs)
+        rep = srv.report()
+        sat[name] = {"mpts_per_s": rep["mpts_per_s"], "seconds": rep["seconds"],
+                     "launches": rep["launches"], "frames": rep["frames"]}
+        srv.close()
+        torch.cuda.empty_cache()
+    sat["serving_vs_plain"] = sat["serving"]["mpts_per_s"] / sat["plain"]["mpts_per_s"]
+    sv, pl = out["serving"], out["plain"]
+    line = {
+        "metric": METRIC, "value": sv["mpts_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": sv["seconds"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"serving-16 octrees ({total} points, scale {args.serving_scale})",
+                   "requests": len(reqs), "request_points": "log-uniform 100k-5M",
+                   "arrival": f"Poisson, {rate / 1e6:.0f} Mpts/s (70% of plain capacity "
+                              f"{cap / 1e6:.0f} Mpts/s)",
+                   "hbm_budget_bytes": budget, "frame": "1920x1080 render of every octree "
+                                                        "every 33.3 ms",
+                   "path": "serving form: HBM-budget admission, continuous batching, "
+                           "2 half-GPU persistent launches in flight",
+                   "inputs": "pinned host memory (copies inside the served latency)"},
+        "latency_ms": {"serving_p50": sv["latency_ms"]["p50"],
+                       "serving_p99": sv["latency_ms"]["p99"],
+                       "plain_p50": pl["latency_ms"]["p50"], "plain_p99": pl["latency_ms"]["p99"]},
+        "serving": sv, "plain": pl, "saturated": sat,
+        "e2e": {"value": sv["mpts_per_s"], "unit": UNIT,
+                "h2d_bytes_per_step": 16 * total, "d2h_bytes_per_step": 0},
+        "gpu_launches": sv["launches"], "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -514,7 +634,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="aerial",
-                    choices=["aerial", "uniform", "clustered", "mixed"])
+                    choices=["aerial", "uniform", "clustered", "mixed", "serving"])
+    ap.add_argument("--serving-scale", type=float, default=0.25,
+                    help="octree sizes of the serving workload relative to 5M-200M points")
     ap.add_argument("--points", type=int, default=None)
     ap.add_argument("--ref-batches", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
@@ -526,6 +648,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

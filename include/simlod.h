@@ -246,6 +246,17 @@ SIMLOD_API int simlod_plan_autotune(simlod_t* h, const simlod_point* const* d_ba
                                     const uint64_t* counts, uint32_t n_batches, void* stream,
                                     simlod_plan_params* best, double* best_ms);
 
+/* Width of the handle's persistent launches (simlod_insert_batches,
+ * simlod_frame_update): blocks_per_sm blocks of 512 threads per SM, from 1 to
+ * *max_blocks_per_sm (what fits on an SM; 0 = that maximum, the default).
+ * A persistent launch waits at its grid barriers for all of its blocks, so
+ * launches of several handles that run at the same time must together fit
+ * (for example two handles at 1 block per SM when 2 fit): launches that
+ * together need more block slots than the GPU has can wait on each other
+ * until their barriers time out (SIMLOD_ERR_TIMEOUT). */
+SIMLOD_API int simlod_set_launch_width(simlod_t* h, uint32_t blocks_per_sm,
+                                       uint32_t* max_blocks_per_sm);
+
 /* Frame-budget update (Section 7.2): as simlod_insert_batches, but before
  * starting batch k > 0 the kernel checks the time since the launch began
  * (the GPU's global timer); once it exceeds budget_ns it stops. Batches are

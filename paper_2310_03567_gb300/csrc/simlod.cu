@@ -126,7 +126,8 @@ struct simlod {
   cudaStream_t last_stream;
   int sm_count;
   // fused form
-  int fused_grid;           // co-resident blocks of k_fused
+  int fused_grid;           // blocks of k_fused launches
+  int fused_max_per_sm;     // co-resident k_fused blocks per SM
   bool mirror_stale;        // a fused launch ran since the last control-block read
   unsigned long long rejected_async_seen;  // fused-launch rejections already reported
   BatchDesc* desc_host;     // pinned staging of the batch table
@@ -606,7 +607,10 @@ SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t are
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_fused, FUSED_BLOCK,
                                                              PHASE_SMEM_BYTES) == cudaSuccess)
-    h->fused_grid = std::min(bpsm, 4) * h->sm_count;
+  {
+    h->fused_max_per_sm = std::min(bpsm, 4);
+    h->fused_grid = h->fused_max_per_sm * h->sm_count;
+  }
   if (cudaMallocHost(reinterpret_cast<void**>(&h->desc_host),
                      sizeof(BatchDesc) * MAX_FUSED_BATCHES) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&h->fctl_host), sizeof(FusedCtl)) != cudaSuccess ||
@@ -762,7 +766,7 @@ SIMLOD_API int simlod_plan_create(simlod_t* h, const simlod_point* const* d_batc
   P->n = n_batches;
   P->total = total;
   P->units = tile0[n_batches];
-  const unsigned per_sm = (unsigned)h->fused_grid / (unsigned)h->sm_count;
+  const unsigned per_sm = (unsigned)h->fused_max_per_sm;
   P->grid = (unsigned)h->sm_count *
             (params->blocks_per_sm ? std::min<unsigned>(params->blocks_per_sm, per_sm) : per_sm);
   P->last = h->last_stream;
@@ -864,7 +868,7 @@ SIMLOD_API int simlod_plan_autotune(simlod_t* h, const simlod_point* const* d_ba
   for (uint64_t m : {1ull << 18, 1ull << 20, 1ull << 21, 1ull << 22, 1ull << 23})
     if (m < mb) merges.push_back(m);
   merges.push_back(mb);
-  const unsigned per_sm = (unsigned)h->fused_grid / std::max(1, h->sm_count);
+  const unsigned per_sm = (unsigned)h->fused_max_per_sm;
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
     return SIMLOD_ERR_CUDA;
@@ -897,6 +901,17 @@ SIMLOD_API int simlod_plan_autotune(simlod_t* h, const simlod_point* const* d_ba
   if (best_t < 0.0) return SIMLOD_ERR_CUDA;
   if (best_ms) *best_ms = best_t;
   return rr;
+}
+
+SIMLOD_API int simlod_set_launch_width(simlod_t* h, uint32_t blocks_per_sm,
+                                       uint32_t* max_blocks_per_sm) {
+  if (!h) return SIMLOD_ERR_INVALID_ARG;
+  if (max_blocks_per_sm) *max_blocks_per_sm = (uint32_t)h->fused_max_per_sm;
+  if (h->fused_max_per_sm < 1) return SIMLOD_ERR_CUDA;
+  if (blocks_per_sm > (uint32_t)h->fused_max_per_sm) return SIMLOD_ERR_INVALID_ARG;
+  const int bps = blocks_per_sm ? (int)blocks_per_sm : h->fused_max_per_sm;
+  h->fused_grid = bps * h->sm_count;
+  return SIMLOD_OK;
 }
 
 SIMLOD_API int simlod_reset(simlod_t* h, void* stream) {

@@ -1,0 +1,259 @@
+"""Serving form: many octrees resident on one GPU, insert requests admitted by
+an HBM budget, continuous batching of each octree's queued requests into one
+persistent launch, and a per-frame render of every octree (Section 6) between
+the updates (Section 7.2's interleaving of updates and frames).
+
+Every octree has its own CUDA stream and arena. A request (points of one
+octree, in pinned host memory) is admitted when its device copy fits the HBM
+budget left by the arenas and the requests in flight; it is copied on its
+octree's stream. When a launch slot is free, the octree with the oldest
+admitted request gets one fused launch (simlod_insert_batches) over all of its
+admitted requests, each request one batch, in arrival order. At most
+`compute_slots` launches are in flight, and each handle's persistent launch
+uses 1 / compute_slots of every SM, so that the launches in flight always fit
+on the GPU together (their grid barriers wait for all of their blocks). Frames
+are enqueued on each octree's stream after the updates before them, so a
+frame shows every request completed before it and none half-applied.
+
+Requests of one octree are applied in arrival order, which fixes their gidx:
+each octree ends up exactly as if its requests had been inserted alone, one
+after another (the tests compare both byte for byte).
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+
+from . import simlod
+
+FRAME_W, FRAME_H = 1920, 1080
+
+
+@dataclasses.dataclass
+class Request:
+    octree: int
+    points: object  # pinned host uint8 tensor [n, 16]
+    arrival: float  # seconds on the server clock
+    rid: int = 0
+    admitted: float = -1.0
+    done: float = -1.0
+    dev: object = None  # device copy while in flight
+
+    @property
+    def n(self) -> int:
+        return int(self.points.shape[0])
+
+    @property
+    def nbytes(self) -> int:
+        return 16 * self.n
+
+
+@dataclasses.dataclass
+class OctreeSpec:
+    cfg: object       # simlod.Config
+    data_bytes: int   # arena data region
+    camera: object = None  # 16 float32 view-projection for its frames
+
+
+class Server:
+    def __init__(self, specs, hbm_budget: int, compute_slots: int = 2, frame_ms: float = 0.0,
+                 max_batches_per_launch: int = 64, plain: bool = False):
+        """plain=True serves with the plain per-kernel path instead: one
+        request per update, one update at a time (the baseline)."""
+        import torch
+        self.torch = torch
+        if compute_slots < 1:
+            raise ValueError("compute_slots must be at least 1")
+        self.plain = plain
+        if plain:
+            compute_slots, max_batches_per_launch = 1, 1
+        self.budget = int(hbm_budget)
+        self.used = 0
+        self.slots = compute_slots
+        self.frame_ms = frame_ms
+        self.max_batches = max_batches_per_launch
+        self.trees, self.cams, self.frames = [], [], []
+        for sp in specs:
+            arena = simlod.make_arena(sp.cfg, sp.data_bytes)
+            self.used += arena.numel()
+            tree = simlod.Octree(sp.cfg, arena, stream=torch.cuda.Stream())
+            mx = tree.set_launch_width(0)
+            if compute_slots > 1:
+                if mx < compute_slots:
+                    raise ValueError(f"{compute_slots} launch slots need {compute_slots} blocks "
+                                     f"per SM; {mx} fit")
+                tree.set_launch_width(mx // compute_slots)
+            self.trees.append(tree)
+            self.cams.append(sp.camera)
+            self.frames.append(None)
+        if self.used > self.budget:
+            raise ValueError("the arenas alone exceed the HBM budget")
+        self.pending = []      # arrived, not admitted (arrival order)
+        self.queued = [[] for _ in self.trees]   # admitted, not launched, per octree
+        self.inflight = []     # (event, octree, requests)
+        self.busy = [False] * len(self.trees)
+        self.finished = []
+        self.frame_times = []
+        self.launches = 0
+        self.t0 = None
+
+    # ------------------------------------------------------------- clock
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    # ------------------------------------------------------------ phases
+    def _poll(self):
+        keep = []
+        for ev, k, reqs in self.inflight:
+            if ev.query():
+                t = self.now()
+                for r in reqs:
+                    r.done = t
+                    r.dev = None
+                    self.used -= r.nbytes
+                    self.finished.append(r)
+                self.busy[k] = False
+            else:
+                keep.append((ev, k, reqs))
+        self.inflight = keep
+
+    def _admit(self):
+        torch = self.torch
+        while self.pending and self.used + self.pending[0].nbytes <= self.budget:
+            r = self.pending.pop(0)
+            tree = self.trees[r.octree]
+            with torch.cuda.stream(tree.stream):
+                r.dev = torch.empty_like(r.points, device="cuda")
+                r.dev.copy_(r.points, non_blocking=True)
+            self.used += r.nbytes
+            r.admitted = self.now()
+            self.queued[r.octree].append(r)
+
+    def _launch(self):
+        torch = self.torch
+        while len(self.inflight) < self.slots:
+            ready = [k for k in range(len(self.trees)) if self.queued[k] and not self.busy[k]]
+            if not ready:
+                return
+            k = min(ready, key=lambda j: self.queued[j][0].arrival)
+            reqs = self.queued[k][: self.max_batches]
+            self.queued[k] = self.queued[k][self.max_batches:]
+            tree = self.trees[k]
+            if self.plain:
+                rc = tree.insert(reqs[0].dev, stream=tree.stream, check=False)
+            else:
+                rc = tree.insert_many_ptrs([r.dev.data_ptr() for r in reqs], [r.n for r in reqs])
+            if rc != simlod.OK:
+                raise simlod.SimlodError(rc, "insert")
+            ev = torch.cuda.Event()
+            ev.record(tree.stream)
+            self.inflight.append((ev, k, reqs))
+            self.busy[k] = True
+            self.launches += 1
+
+    def render_frame(self):
+        """Render every octree into its own frame on its stream; returns the
+        frame's completion events."""
+        torch = self.torch
+        evs = []
+        for k, tree in enumerate(self.trees):
+            if self.cams[k] is None:
+                continue
+            if self.frames[k] is None:
+                with torch.cuda.stream(tree.stream):
+                    self.frames[k] = torch.empty((FRAME_H, FRAME_W), dtype=torch.int64,
+                                                 device="cuda")
+            tree.render(self.cams[k], self.frames[k])
+            ev = torch.cuda.Event()
+            ev.record(tree.stream)
+            evs.append(ev)
+        return evs
+
+    # --------------------------------------------------------------- run
+    def run(self, requests, idle_sleep: float = 5e-5):
+        """Serve `requests` (sorted by arrival) in real time; returns the
+        finished requests."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        room = self.budget - sum(t.arena.numel() for t in self.trees)
+        for i, r in enumerate(reqs):
+            r.rid = i
+            if r.nbytes > room:
+                raise ValueError(f"request {i} ({r.nbytes} bytes) can never fit the HBM budget")
+        self.t0 = time.perf_counter()
+        nxt = 0
+        next_frame = self.frame_ms / 1e3 if self.frame_ms else None
+        frame_evs, frame_t = [], 0.0
+        while nxt < len(reqs) or self.pending or any(self.queued) or self.inflight:
+            t = self.now()
+            while nxt < len(reqs) and reqs[nxt].arrival <= t:
+                self.pending.append(reqs[nxt])
+                nxt += 1
+            self._poll()
+            self._admit()
+            self._launch()
+            if next_frame is not None and t >= next_frame and not frame_evs:
+                frame_evs, frame_t = self.render_frame(), t
+                next_frame += self.frame_ms / 1e3
+            if frame_evs and all(e.query() for e in frame_evs):
+                self.frame_times.append(self.now() - frame_t)
+                frame_evs = []
+            time.sleep(idle_sleep)
+        for e in frame_evs:
+            e.synchronize()
+        for tree in self.trees:
+            rc = tree.sync()
+            if rc != simlod.OK:
+                raise simlod.SimlodError(rc, "serving sync")
+        return self.finished
+
+    def report(self) -> dict:
+        lat = np.array([r.done - r.arrival for r in self.finished]) * 1e3
+        wait = np.array([r.admitted - r.arrival for r in self.finished]) * 1e3
+        pts = sum(r.n for r in self.finished)
+        span = max(r.done for r in self.finished) - min(r.arrival for r in self.finished)
+        ft = np.array(self.frame_times) * 1e3 if self.frame_times else np.zeros(1)
+        return {"requests": len(self.finished), "points": pts, "seconds": span,
+                "mpts_per_s": pts / span / 1e6 if span > 0 else 0.0,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                               "p99": float(np.percentile(lat, 99))},
+                "admission_wait_ms": {"p50": float(np.percentile(wait, 50)),
+                                      "p99": float(np.percentile(wait, 99))},
+                "launches": self.launches, "frames": len(self.frame_times),
+                "frame_ms": {"p50": float(np.percentile(ft, 50)),
+                             "p99": float(np.percentile(ft, 99))}}
+
+    def close(self):
+        for t in self.trees:
+            t.close()
+
+
+def poisson_requests(streams, sizes_lo: int, sizes_hi: int, rate_pts_per_s: float, seed: int):
+    """Cut each octree's point stream (pinned uint8 tensors [n, 16]) into
+    requests with log-uniform sizes in [sizes_lo, sizes_hi], and give them
+    Poisson arrival times whose mean point rate is rate_pts_per_s; each
+    arrival takes the next request of an octree drawn in proportion to its
+    points left. Returns the requests, sorted by arrival."""
+    rng = np.random.default_rng(seed)
+    cuts = []
+    for k, s in enumerate(streams):
+        n, o, parts = int(s.shape[0]), 0, []
+        while o < n:
+            m = int(np.exp(rng.uniform(np.log(sizes_lo), np.log(sizes_hi))))
+            m = min(max(m, 1), n - o)
+            parts.append((o, m))
+            o += m
+        cuts.append(parts)
+    left = np.array([len(c) for c in cuts], float)
+    pos = [0] * len(streams)
+    mean_size = np.mean([m for c in cuts for _, m in c]) if any(cuts) else 1.0
+    t, out = 0.0, []
+    while left.sum() > 0:
+        t += rng.exponential(mean_size / rate_pts_per_s)
+        k = int(rng.choice(len(streams), p=left / left.sum()))
+        o, m = cuts[k][pos[k]]
+        pos[k] += 1
+        left[k] -= 1
+        out.append(Request(octree=k, points=streams[k][o:o + m], arrival=t))
+    return out

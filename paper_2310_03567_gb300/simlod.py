@@ -119,6 +119,7 @@ SIGNATURES = {
     "simlod_sample_node_noalloc": (_I32, [_P, _U64, ctypes.POINTER(ctypes.c_int32), _U32, _U32,
                                           _P, _U64, _P, _P]),
     "simlod_render": (_I32, [_P, _P, _U32, _U32, _P, _I32, _P]),
+    "simlod_set_launch_width": (_I32, [_P, _U32, ctypes.POINTER(_U32)]),
     "simlod_plan_create": (_I32, [_P, _P, _P, _U32, _P, ctypes.POINTER(_P)]),
     "simlod_plan_run": (_I32, [_P, _P]),
     "simlod_plan_info": (_I32, [_P, _P, ctypes.POINTER(_U32)]),
@@ -389,6 +390,15 @@ class Octree:
                                      framebuffer.data_ptr(), int(clear), _stream_ptr(st))
         if rc != OK:
             raise SimlodError(rc, "simlod_render")
+
+    def set_launch_width(self, blocks_per_sm: int) -> int:
+        """Blocks per SM of this handle's persistent launches (0 = all that
+        fit); returns the maximum that fits."""
+        mx = ctypes.c_uint32()
+        rc = self._lib.simlod_set_launch_width(self._h, blocks_per_sm, ctypes.byref(mx))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_set_launch_width")
+        return int(mx.value)
 
     def plan(self, ptrs, counts, merge_points: int = 0, blocks_per_sm: int = 0,
              use_graph: bool = True) -> "Plan":
