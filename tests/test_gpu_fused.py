@@ -196,3 +196,17 @@ def test_fused_capacity_errors_poison(what):
     t.reset()
     assert fused_insert(t, [pts[:100]]) == simlod.OK
     assert_snapshots_equal(t.snapshot(), oracle.static_build(ocfg(**kw), pts[:100]))
+
+
+def test_fused_reads_batches_from_pinned_host_memory():
+    """Host ingest without a staging copy: the persistent kernel reads the
+    batches from pinned host memory over the CPU-GPU link."""
+    w = synth.aerial_workload(n=3_000_000)
+    host = torch.from_numpy(np.ascontiguousarray(w.points).view(np.uint8).reshape(-1, 16))
+    host = host.pin_memory()
+    t = make_tree(1 << 30, root_log2=22)
+    ptrs = [host.data_ptr() + int(o) * 16 for o in w.offsets]
+    assert t.insert_many_ptrs(ptrs, [int(c) for c in w.counts]) == simlod.OK
+    assert t.sync() == simlod.OK
+    assert_snapshots_equal(t.snapshot(),
+                           oracle.static_build(oracle.Config.make(root_log2=22), w.points))
