@@ -72,8 +72,11 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def make_workload(name: str, points: int | None):
+def make_workload(name: str, points: int | None, morton: bool = False):
     from paper_2310_03567_gb300 import synth
+    if morton:
+        w, root = make_workload(name, points)
+        return synth.morton_workload(w), root
     if name == "aerial":
         return synth.aerial_workload(n=points or 50_000_000), 22
     if name == "uniform":
@@ -202,7 +205,7 @@ def run_reference(args):
     return 0
 
 
-def make_octree(w, root_log2: int):
+def make_octree(w, root_log2: int, chunk_points: int = 1000):
     """The octree the bench times for workload w (its capacities follow the
     workload's largest batch); the full-size tests build the same one."""
     import torch
@@ -215,19 +218,20 @@ def make_octree(w, root_log2: int):
                                 max_batch_points=max_batch,
                                 spill_capacity=max(8 << 20, 2 * max_batch),
                                 backlog_capacity=max(2 << 20, 2 * max_batch),
-                                max_nodes=1 << 21)
-    data_bytes = max(256 << 20, w.n_points * 80)
+                                max_nodes=1 << 21, chunk_points=chunk_points)
+    # plus the part-filled last chunk of up to 64k nodes
+    data_bytes = max(256 << 20, w.n_points * 80) + (1 << 16) * 20 * chunk_points
     arena = simlod.make_arena(cfg, data_bytes)
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
     return simlod.Octree(cfg, arena, stream=stream)
 
 
-def rank_workload(name: str, points, rank: int):
+def rank_workload(name: str, points, rank: int, morton: bool = False):
     """The workload a rank builds: every rank has its own octree and stream
     (independent units, no data-path collective); rank r > 0 gets its own
     seed so that the replicas are not copies."""
-    w, root_log2 = make_workload(name, points)
+    w, root_log2 = make_workload(name, points, morton)
     if rank:
         from paper_2310_03567_gb300 import synth
         if name == "aerial":
@@ -276,7 +280,7 @@ def run_ours(args):
     simlod.load()
 
     # each rank builds its own octree from its own stream (independent units)
-    w, root_log2 = rank_workload(args.workload, args.points, rank)
+    w, root_log2 = rank_workload(args.workload, args.points, rank, args.morton)
     n_points = w.n_points
     dev_pts = simlod.points_tensor(w.points)
     ptrs = [dev_pts.data_ptr() + int(o) * 16 for o in w.offsets]
@@ -663,6 +667,73 @@ def run_serving(args):
     return 0
 
 
+def run_chunk_sweep(args):
+    """Chunk-size study (the paper's chunk-size table, Section 7): the fused
+    update of the workload and one 1080p frame for several points-per-chunk,
+    with the data region each needs."""
+    import torch
+
+    from paper_2310_03567_gb300 import simlod
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    simlod.load()
+    w, root_log2 = make_workload(args.workload, args.points, args.morton)
+    dev_pts = simlod.points_tensor(w.points)
+    ptrs = [dev_pts.data_ptr() + int(o) * 16 for o in w.offsets]
+    counts = [int(c) for c in w.counts]
+    side = float(1 << root_log2)
+    ctr = np.asarray(w.root_min, float) + side * np.array([0.5, 0.5, 0.02])
+    cam = simlod.view_proj(ctr + side * np.array([-0.45, -0.55, 0.35]), ctr, 60.0, 1920 / 1080)
+    rows = []
+    for C in (250, 500, 1000, 2000, 5000, 10000):
+        tree = make_octree(w, root_log2, chunk_points=C)
+        st_ = tree.stream
+        for _ in range(args.warmup):
+            tree.reset()
+            if tree.insert_many_ptrs(ptrs, counts) != simlod.OK:
+                raise RuntimeError("insert_batches")
+        if tree.sync() != simlod.OK:
+            raise RuntimeError(f"chunk {C}: update failed")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st_)
+        for _ in range(args.steps):
+            tree.reset()
+            tree.insert_many_ptrs(ptrs, counts)
+        e1.record(st_)
+        torch.cuda.synchronize()
+        if tree.sync() != simlod.OK:
+            raise RuntimeError(f"chunk {C}: update failed")
+        ms = e0.elapsed_time(e1) / args.steps
+        st = tree.stats()
+        frame = torch.empty((1080, 1920), dtype=torch.int64, device="cuda")
+        tree.render(cam, frame)
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        r0.record(st_)
+        for _ in range(3):
+            tree.render(cam, frame)
+        r1.record(st_)
+        torch.cuda.synchronize()
+        payload = 20 * (st["points"] + st["voxels"])
+        rows.append({"chunk_points": C, "mpts_per_s": w.n_points / ms / 1e3, "ms_per_step": ms,
+                     "render_ms": r0.elapsed_time(r1) / 3, "data_used_bytes": st["data_used"],
+                     "records_bytes": payload, "overhead": st["data_used"] / payload - 1.0,
+                     "chunks": st["chunks_bumped"]})
+        tree.close()
+        del frame
+        torch.cuda.empty_cache()
+    base = next(r for r in rows if r["chunk_points"] == 1000)
+    line = {"metric": METRIC, "value": base["mpts_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": w.name, "study": "points per chunk",
+                                            "path": "fused persistent launch per step"},
+            "chunk_sweep": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -677,6 +748,10 @@ def main():
     ap.add_argument("--ref-batches", type=int, default=2)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--chunk-sweep", action="store_true",
+                    help="chunk-size study instead of the standard measurement")
+    ap.add_argument("--morton", action="store_true",
+                    help="sort the workload's stream in Morton order before cutting it")
     ap.add_argument("--batched", action="store_true",
                     help="also time the batched form (always on for --workload mixed)")
     args = ap.parse_args()
@@ -686,6 +761,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.chunk_sweep:
+        return run_chunk_sweep(args)
     return run_ours(args)
 
 

@@ -237,3 +237,32 @@ def mixed_workload(n: int = 100_000_000, seed: int = 3, batch_lo: int = 65_536,
                     f"seed {seed}; {half} terrain + {n - half} clustered points over a 4 km "
                     f"square, alternating runs of 1M-10M; batches log-uniform in "
                     f"[{batch_lo},{batch_hi}]; root [0,2^22)^3 mm")
+
+
+def _spread3(v: np.ndarray) -> np.ndarray:
+    """Bits 0..20 of v to bits 0, 3, 6, ..., 60 (Morton interleave)."""
+    v = v.astype(np.uint64) & np.uint64(0x1FFFFF)
+    v = (v | (v << np.uint64(32))) & np.uint64(0x1F00000000FFFF)
+    v = (v | (v << np.uint64(16))) & np.uint64(0x1F0000FF0000FF)
+    v = (v | (v << np.uint64(8))) & np.uint64(0x100F00F00F00F00F)
+    v = (v | (v << np.uint64(4))) & np.uint64(0x10C30C30C30C30C3)
+    v = (v | (v << np.uint64(2))) & np.uint64(0x1249249249249249)
+    return v
+
+
+def morton_workload(w: Workload) -> Workload:
+    """The same points and batch sizes, with the stream sorted in Morton
+    (z-curve) order of the top 21 bits of each coordinate relative to the root
+    (the paper's Morton-ordered input variant)."""
+    pts = w.stream()
+    shift = np.uint64(max(0, w.root_log2 - 21))
+    key = np.zeros(len(pts), np.uint64)
+    for a, f in enumerate("xyz"):
+        rel = (pts[f].astype(np.int64) - int(w.root_min[a])).astype(np.uint64) >> shift
+        key |= _spread3(rel) << np.uint64(a)
+    order = np.argsort(key, kind="stable")
+    sorted_pts = pts[order]
+    cnt = w.counts.copy()
+    off = np.concatenate([[0], np.cumsum(cnt)[:-1]]).astype(np.uint64)
+    return Workload(w.name + "-morton", sorted_pts, off, cnt, w.root_min, w.root_log2,
+                    w.recipe + "; stream sorted in Morton order, same batch sizes in order")

@@ -210,3 +210,13 @@ def test_fused_reads_batches_from_pinned_host_memory():
     assert t.sync() == simlod.OK
     assert_snapshots_equal(t.snapshot(),
                            oracle.static_build(oracle.Config.make(root_log2=22), w.points))
+
+
+def test_morton_ordered_stream():
+    """The Morton-ordered input variant (dense, strongly local batches)."""
+    w = synth.morton_workload(synth.clustered_workload(n=4_000_000, n_quads=300,
+                                                       batch_lo=200_000, batch_hi=1_000_000))
+    t = make_tree(2 << 30, root_log2=21)
+    assert fused_insert(t, list(w.batches())) == simlod.OK
+    assert_snapshots_equal(t.snapshot(),
+                           oracle.static_build(oracle.Config.make(root_log2=21), w.stream()))
