@@ -306,6 +306,21 @@ SIMLOD_API int simlod_snapshot(simlod_t* h, simlod_snapshot_t* snap);
 SIMLOD_API int simlod_render(simlod_t* h, const float view_proj[16], uint32_t width,
                              uint32_t height, uint64_t* d_framebuffer, int clear, void* stream);
 
+/* Restore a canonical snapshot (as simlod_snapshot writes it, or the same
+ * layout from elsewhere) into h, replacing its octree: nodes, their chunk
+ * lists (a leaf's points keep their gidx, an inner node's voxels their cell
+ * and colour), occupancy grids from the voxel cells, and the gidx counter at
+ * the number of points, so that later inserts continue the stream exactly as
+ * on the octree the snapshot was taken from. The configuration of h must be
+ * the snapshot's (root cube, T, C, G); a snapshot that does not form one
+ * octree of it (unsorted or missing nodes, wrong chunk counts, cells off the
+ * grid) is rejected with SIMLOD_ERR_INVALID_ARG and h is unchanged;
+ * SIMLOD_ERR_NODES_FULL / SIMLOD_ERR_ARENA_FULL when it does not fit. The
+ * octree is rebuilt on the host and copied in; the call waits for `stream`
+ * and returns when the copies are done. Statistics restart (points and
+ * voxels are set to the snapshot's). */
+SIMLOD_API int simlod_restore(simlod_t* h, const simlod_snapshot_t* snap, void* stream);
+
 /* Record CUDA events around every kernel launch (on the launching stream)
  * and accumulate per-kernel device time; enable = 0 stops, clear resets. */
 SIMLOD_API int simlod_set_timing(simlod_t* h, int enable, int clear);

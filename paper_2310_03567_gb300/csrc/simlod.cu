@@ -914,6 +914,197 @@ SIMLOD_API int simlod_set_launch_width(simlod_t* h, uint32_t blocks_per_sm,
   return SIMLOD_OK;
 }
 
+// ----------------------------------------------------------------- restore
+
+SIMLOD_API int simlod_restore(simlod_t* h, const simlod_snapshot_t* snap, void* stream) {
+  if (!h || !snap || !snap->nodes || snap->n_nodes == 0 || (snap->n_points && !snap->points) ||
+      (snap->n_voxels && !snap->voxels))
+    return SIMLOD_ERR_INVALID_ARG;
+  const simlod_config& g = h->cfg;
+  const uint64_t n = snap->n_nodes;
+  if (n > g.max_nodes) return SIMLOD_ERR_NODES_FULL;
+  if (snap->n_points > (1ull << 32)) return SIMLOD_ERR_TOO_MANY_POINTS;
+  const simlod_node_rec* nodes = snap->nodes;
+  const uint32_t C = g.chunk_points, G = g.grid_log2;
+  // canonical key (level, ix, iy, iz) of a record; records must be sorted by it
+  struct Key {
+    uint64_t level, ix, iy, iz;
+    bool operator<(const Key& o) const {
+      if (level != o.level) return level < o.level;
+      if (ix != o.ix) return ix < o.ix;
+      if (iy != o.iy) return iy < o.iy;
+      return iz < o.iz;
+    }
+    bool operator==(const Key& o) const {
+      return level == o.level && ix == o.ix && iy == o.iy && iz == o.iz;
+    }
+  };
+  std::vector<Key> keys(n);
+  std::vector<uint64_t> po(n + 1, 0), vo(n + 1, 0);
+  for (uint64_t k = 0; k < n; ++k) {
+    const simlod_node_rec& r = nodes[k];
+    if (r.level > g.root_log2 || r.log2size != g.root_log2 - r.level) return SIMLOD_ERR_INVALID_ARG;
+    const uint32_t L = r.log2size;
+    uint64_t ijk[3];
+    for (int a = 0; a < 3; ++a) {
+      const long long rel = (long long)r.min[a] - g.root_min[a];
+      if (rel < 0 || (rel & ((1ll << L) - 1)) || (rel >> g.root_log2)) return SIMLOD_ERR_INVALID_ARG;
+      ijk[a] = (uint64_t)(rel >> L);
+    }
+    keys[k] = Key{r.level, ijk[0], ijk[1], ijk[2]};
+    if (k && !(keys[k - 1] < keys[k])) return SIMLOD_ERR_INVALID_ARG;
+    const uint64_t cnt = r.is_inner ? r.n_voxels : r.n_points;
+    if ((r.is_inner ? r.n_points : r.n_voxels) != 0 || r.n_chunks != (cnt + C - 1) / C ||
+        (r.is_inner && L == 0))
+      return SIMLOD_ERR_INVALID_ARG;
+    po[k + 1] = po[k] + r.n_points;
+    vo[k + 1] = vo[k] + r.n_voxels;
+  }
+  if (po[n] != snap->n_points || vo[n] != snap->n_voxels || keys[0].level != 0)
+    return SIMLOD_ERR_INVALID_ARG;
+  auto find = [&](const Key& k) -> int64_t {
+    auto it = std::lower_bound(keys.begin(), keys.end(), k);
+    return (it != keys.end() && *it == k) ? (int64_t)(it - keys.begin()) : -1;
+  };
+  // node ids: the children of a node are 8 consecutive ids in octant order
+  std::vector<uint32_t> rec_of;
+  std::vector<uint32_t> first_child(n, NONE);
+  rec_of.reserve(n);
+  rec_of.push_back(0);
+  for (size_t q = 0; q < rec_of.size(); ++q) {
+    const uint32_t r = rec_of[q];
+    if (!nodes[r].is_inner) continue;
+    first_child[q] = (uint32_t)rec_of.size();
+    const Key& pk = keys[r];
+    for (uint32_t o = 0; o < 8; ++o) {
+      const int64_t c = find(Key{pk.level + 1, 2 * pk.ix + (o & 1), 2 * pk.iy + ((o >> 1) & 1),
+                                 2 * pk.iz + ((o >> 2) & 1)});
+      if (c < 0 || rec_of.size() >= n) return SIMLOD_ERR_INVALID_ARG;
+      rec_of.push_back((uint32_t)c);
+    }
+  }
+  if (rec_of.size() != n) return SIMLOD_ERR_INVALID_ARG;  // nodes outside the tree
+  // host image of the node arrays and of the used data region (bump order)
+  const uint64_t cb = chunk_bytes_of(&g), gb = grid_bytes_of(&g), db = dir_bytes_of(&g);
+  const uint32_t dcap = dir_cap_of(&g);
+  uint64_t bytes = 0, chunks = 0;
+  for (uint64_t k = 0; k < n; ++k) {
+    bytes += nodes[k].is_inner ? gb : db;
+    bytes += nodes[k].n_chunks * cb;
+    chunks += nodes[k].n_chunks;
+  }
+  if (bytes > h->lay.data_bytes) return SIMLOD_ERR_ARENA_FULL;
+  if (chunks > h->lay.max_chunks) return SIMLOD_ERR_ARENA_FULL;
+  std::vector<uint8_t> data;
+  try {
+    data.assign(bytes, 0);
+  } catch (const std::bad_alloc&) {
+    return SIMLOD_ERR_INVALID_ARG;
+  }
+  std::vector<uint32_t> child(n), gridref(n), num(n), zeros(n, 0);
+  std::vector<NodeMeta> meta(n);
+  uint64_t bump = 0;
+  auto take = [&](uint64_t b) {
+    const uint64_t at = bump;
+    bump += b;
+    return at;
+  };
+  for (uint64_t id = 0; id < n; ++id) {
+    const uint32_t r = rec_of[id];
+    const simlod_node_rec& rec = nodes[r];
+    NodeMeta m;
+    memset(&m, 0, sizeof(m));
+    for (int a = 0; a < 3; ++a) m.min[a] = rec.min[a];
+    m.level = rec.level;
+    m.st_tail = NONE;
+    m.head = m.tail = NONE;
+    uint32_t* dir = nullptr;
+    if (rec.is_inner) {
+      const uint64_t go = take(gb);
+      uint32_t* words = reinterpret_cast<uint32_t*>(data.data() + go);
+      for (uint64_t q = vo[r]; q < vo[r + 1]; ++q) {
+        const uint32_t cell = snap->voxels[q].cell;
+        if (cell >> (3 * G)) return SIMLOD_ERR_INVALID_ARG;
+        words[cell >> 5] |= 1u << (cell & 31u);
+      }
+      gridref[id] = (uint32_t)(go / REF_BYTES);
+      child[id] = first_child[id];
+      num[id] = (uint32_t)rec.n_voxels;
+      m.dir = NONE;
+    } else {
+      const uint64_t d = take(db);
+      dir = reinterpret_cast<uint32_t*>(data.data() + d);
+      gridref[id] = NONE;
+      child[id] = NONE;
+      num[id] = (uint32_t)rec.n_points;
+      m.dir = (uint32_t)(d / REF_BYTES);
+    }
+    const uint64_t cnt = rec.is_inner ? rec.n_voxels : rec.n_points;
+    uint32_t prev = NONE;
+    for (uint64_t j = 0; j < rec.n_chunks; ++j) {
+      const uint64_t co = take(cb);
+      const uint32_t ref = (uint32_t)(co / REF_BYTES);
+      uint8_t* ch = data.data() + co;
+      *reinterpret_cast<uint32_t*>(ch) = NONE;
+      int4* recs = reinterpret_cast<int4*>(ch + CHUNK_HEADER);
+      uint32_t* aux = reinterpret_cast<uint32_t*>(ch + CHUNK_HEADER + 16ull * C);
+      for (uint64_t q = 0; q < C && j * C + q < cnt; ++q) {
+        if (rec.is_inner) {
+          const simlod_voxel_rec& v = snap->voxels[vo[r] + j * C + q];
+          recs[q] = make_int4(v.x, v.y, v.z, (int)v.rgba);
+          aux[q] = v.cell;
+        } else {
+          const simlod_point_rec& p = snap->points[po[r] + j * C + q];
+          recs[q] = make_int4(p.x, p.y, p.z, (int)p.rgba);
+          aux[q] = p.gidx;
+        }
+      }
+      if (prev == NONE) m.head = ref;
+      else *reinterpret_cast<uint32_t*>(data.data() + (uint64_t)prev * REF_BYTES) = ref;
+      if (dir && j < dcap) dir[j] = ref;
+      prev = ref;
+    }
+    m.tail = prev;
+    m.n_chunks = (uint32_t)rec.n_chunks;
+    meta[id] = m;
+  }
+  // start from an empty octree (clears a poisoned state and the claim table)
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool dirty = h->sticky != 0;
+  if (dirty) cudaStreamSynchronize(h->last_stream);
+  h->sticky = 0;
+  int rc = init_octree(h, s, true, false);
+  if (rc) return poison(h, rc);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return poison(h, SIMLOD_ERR_CUDA);
+  Ctl t;
+  if (cudaMemcpy(&t, h->ctx.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return poison(h, SIMLOD_ERR_CUDA);
+  t.base = snap->n_points;
+  t.n_nodes = (unsigned int)n;
+  t.bump = bump;
+  t.chunks_bumped = chunks;
+  t.pool_top = 0;
+  t.st_points = snap->n_points;
+  t.st_voxels = snap->n_voxels;
+  const Ctx& c = h->ctx;
+  if (cudaMemcpy(c.child, child.data(), 4 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c.gridref, gridref.data(), 4 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c.num, num.data(), 4 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c.cnt, zeros.data(), 4 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c.scur, zeros.data(), 4 * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c.meta, meta.data(), sizeof(NodeMeta) * n, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      (bump && cudaMemcpy(c.data, data.data(), bump, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(c.ctl, &t, sizeof(Ctl), cudaMemcpyHostToDevice) != cudaSuccess)
+    return poison(h, SIMLOD_ERR_CUDA);
+  h->base = snap->n_points;
+  h->n_nodes = (uint32_t)n;
+  h->mirror_stale = false;
+  h->rejected_async_seen = 0;
+  h->last_stream = s;
+  return SIMLOD_OK;
+}
+
 SIMLOD_API int simlod_reset(simlod_t* h, void* stream) {
   if (!h) return SIMLOD_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -120,6 +120,7 @@ SIGNATURES = {
                                           _P, _U64, _P, _P]),
     "simlod_render": (_I32, [_P, _P, _U32, _U32, _P, _I32, _P]),
     "simlod_set_launch_width": (_I32, [_P, _U32, ctypes.POINTER(_U32)]),
+    "simlod_restore": (_I32, [_P, ctypes.POINTER(Snapshot_t), _P]),
     "simlod_plan_create": (_I32, [_P, _P, _P, _U32, _P, ctypes.POINTER(_P)]),
     "simlod_plan_run": (_I32, [_P, _P]),
     "simlod_plan_info": (_I32, [_P, _P, ctypes.POINTER(_U32)]),
@@ -390,6 +391,22 @@ class Octree:
                                      framebuffer.data_ptr(), int(clear), _stream_ptr(st))
         if rc != OK:
             raise SimlodError(rc, "simlod_render")
+
+    def restore(self, snap, stream=None) -> None:
+        """Replace the octree with a canonical snapshot (this library's or the
+        oracle's: same record layout); see simlod_restore."""
+        nodes = np.ascontiguousarray(snap.nodes)
+        points = np.ascontiguousarray(snap.points)
+        voxels = np.ascontiguousarray(snap.voxels)
+        s = Snapshot_t()
+        s.nodes, s.nodes_capacity = nodes.ctypes.data, len(nodes)
+        s.points, s.points_capacity = points.ctypes.data if len(points) else None, len(points)
+        s.voxels, s.voxels_capacity = voxels.ctypes.data if len(voxels) else None, len(voxels)
+        s.n_nodes, s.n_points, s.n_voxels = len(nodes), len(points), len(voxels)
+        st = stream if stream is not None else self.stream
+        rc = self._lib.simlod_restore(self._h, ctypes.byref(s), _stream_ptr(st))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_restore")
 
     def set_launch_width(self, blocks_per_sm: int) -> int:
         """Blocks per SM of this handle's persistent launches (0 = all that
