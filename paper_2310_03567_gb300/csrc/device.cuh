@@ -63,6 +63,9 @@ constexpr uint32_t CHUNK_HEADER = 16;
 #ifndef SL_PHASE_MIN_BLOCKS
 #define SL_PHASE_MIN_BLOCKS 2
 #endif
+#ifndef SL_COUNT_UNROLL
+#define SL_COUNT_UNROLL 1
+#endif
 #ifndef SL_STORE_UNROLL
 #define SL_STORE_UNROLL 2
 #endif
@@ -73,6 +76,7 @@ constexpr uint32_t NODE_CACHE = SL_NODE_CACHE;         // nodes mirrored in shar
 constexpr uint32_t NODE_CACHE_BYTES = NODE_CACHE * 8;  // child + grid reference
 constexpr uint32_t ZERO_UNIT = 4096;                   // bytes of grid zeroed per warp unit
 constexpr int DESCENT_GROUP = SL_DESCENT_GROUP;        // levels whose grid words load together
+constexpr int COUNT_U = SL_COUNT_UNROLL;               // count units a warp carries at a time
 constexpr uint32_t WBUF = 64;                          // new-cell slots staged per warp
 constexpr int PHASE_BLOCK = SL_PHASE_BLOCK;            // threads of count / advance / fused blocks
 constexpr int PHASE_MIN_BLOCKS = SL_PHASE_MIN_BLOCKS;  // resident blocks per SM they aim for
@@ -398,6 +402,54 @@ __device__ bool hash_claim_rest(const Ctx& c, unsigned long long key, unsigned l
   return false;
 }
 
+// ------------------------------------------------ lane runs (warp groups)
+//
+// Lanes that hold the same value in a contiguous run of participating lanes
+// form one group: one shuffle and two ballots, instead of a match over the
+// whole warp. Equal values in separate runs form separate groups, which every
+// caller tolerates (more groups, same result: counts and slot reservations
+// add up, claims of one cell meet again in the table). The points a warp
+// holds are neighbours in the stream, so equal nodes and cells mostly sit in
+// runs.
+struct LaneRun {
+  bool head;       // this lane starts its run
+  uint32_t first;  // the lane that starts this lane's run
+  uint32_t end;    // one past the run's last lane
+};
+
+__device__ __forceinline__ unsigned lanes_upto(uint32_t lane) {
+  return lane == 31u ? FULL_MASK : (2u << lane) - 1u;
+}
+
+// All 32 lanes call; lanes without `on` take part in no run.
+template <typename T>
+__device__ __forceinline__ LaneRun lane_run(bool on, T v) {
+  const uint32_t lane = lane_id();
+  const unsigned onm = __ballot_sync(FULL_MASK, on);
+  const T prev = __shfl_up_sync(FULL_MASK, v, 1);
+  const bool head = on && !(lane > 0u && ((onm >> (lane - 1u)) & 1u) && prev == v);
+  const unsigned heads = __ballot_sync(FULL_MASK, head);
+  LaneRun r;
+  r.head = head;
+  const unsigned below = heads & lanes_upto(lane);
+  r.first = below ? 31u - (uint32_t)__clz(below) : lane;
+  const unsigned breaks = (heads | ~onm) & ~lanes_upto(r.first);
+  r.end = breaks ? (uint32_t)__ffs(breaks) - 1u : 32u;
+  return r;
+}
+
+// All 32 lanes call: the minimum of v over this lane and the lanes after it
+// in its run (at the run's first lane: the run's minimum).
+__device__ __forceinline__ unsigned long long run_min(unsigned long long v, const LaneRun& r) {
+  const uint32_t lane = lane_id();
+#pragma unroll
+  for (uint32_t d = 1; d < 32u; d <<= 1) {
+    const unsigned long long o = __shfl_down_sync(FULL_MASK, v, d);
+    if (lane + d < r.end && o < v) v = o;
+  }
+  return v;
+}
+
 // Per-warp staging of the table slots of new cells (shared memory), flushed
 // to the backlog with one atomic per flush.
 struct WarpBuf {
@@ -525,10 +577,10 @@ __device__ __forceinline__ void warp_claim_global(const Ctx& c, WarpBuf& wb, con
     if (mi == 0u) continue;
     const uint32_t ni = (uint32_t)__popc(mi);
     if (wb.n + ni > WBUF) warp_flush(c, wb);
+    const LaneRun r = lane_run(inst[j], node[j]);
     if (inst[j]) {
       wb.buf[wb.n + __popc(mi & ((1u << lane) - 1u))] = h[j];
-      const unsigned gm = __match_any_sync(mi, node[j]);
-      if ((int)lane == __ffs(gm) - 1) tally_add(c, wb.smem, node[j], (uint32_t)__popc(gm));
+      if (r.head) tally_add(c, wb.smem, node[j], r.end - lane);
     }
     wb.n += ni;
   }
@@ -536,9 +588,10 @@ __device__ __forceinline__ void warp_claim_global(const Ctx& c, WarpBuf& wb, con
 
 // All 32 lanes call. For each of N items j, lanes with want[j] contend for
 // the cell key[j] = (node[j], cell) with val = (gidx << 32 | rgba); the lowest
-// gidx wins. Lanes with equal keys are merged first and only the lowest gidx
-// goes to the global table.
-template <int N>
+// gidx wins. Lanes with equal keys in a run are merged first and only the
+// run's lowest gidx goes to the global table. SORTED: gidx grows with the
+// lane, so a run's first lane holds its lowest gidx.
+template <int N, bool SORTED>
 __device__ __forceinline__ void warp_claim(const Ctx& c, WarpBuf& wb, const bool (&want)[N],
                                            const unsigned long long (&key)[N],
                                            const uint32_t (&gidx)[N], const uint32_t (&rgba)[N],
@@ -551,44 +604,20 @@ __device__ __forceinline__ void warp_claim(const Ctx& c, WarpBuf& wb, const bool
   unsigned long long val[N];
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    const unsigned m = __ballot_sync(FULL_MASK, want[j]);
-    lead[j] = false;
     val[j] = ((unsigned long long)gidx[j] << 32) | rgba[j];
-    if (want[j]) {
-      const unsigned grp = __match_any_sync(m, key[j]);
-      lead[j] = __reduce_min_sync(grp, gidx[j]) == gidx[j];
-    }
+    const LaneRun r = lane_run(want[j], key[j]);
+    if (!SORTED) val[j] = run_min(want[j] ? val[j] : ~0ull, r);
+    lead[j] = want[j] && r.head;
   }
   warp_claim_global<N>(c, wb, lead, key, val, node);
 }
 
-// All 32 lanes call. Lanes with `valid` count one point into `leaf` (a
-// reduction per distinct leaf of the warp; the slot is given at store).
+// All 32 lanes call. Lanes with `valid` count one point into `leaf` (one
+// addition per run of equal leaves; the slot is given at store).
 __device__ __forceinline__ void warp_tally(const Ctx& c, uint32_t* smem, bool valid,
                                            uint32_t leaf) {
-  const unsigned m = __ballot_sync(FULL_MASK, valid);
-  if (valid) {
-    const unsigned grp = __match_any_sync(m, leaf);
-    if ((int)lane_id() == __ffs(grp) - 1) tally_add(c, smem, leaf, (uint32_t)__popc(grp));
-  }
-}
-
-// All 32 lanes call. Lanes with `valid` take the next free slot of `node`
-// in this update: its stored count before the update + a running cursor.
-__device__ __forceinline__ uint32_t warp_slot(const Ctx& c, bool valid, uint32_t node) {
-  const uint32_t lane = lane_id();
-  const unsigned m = __ballot_sync(FULL_MASK, valid);
-  uint32_t base = 0, rank = 0;
-  int leader = 0;
-  if (valid) {
-    const unsigned grp = __match_any_sync(m, node);
-    leader = __ffs(grp) - 1;
-    rank = __popc(grp & ((1u << lane) - 1u));
-    if ((int)lane == leader)
-      base = c.meta[node].st_base + atomicAdd(&c.scur[node], (uint32_t)__popc(grp));
-  }
-  base = __shfl_sync(FULL_MASK, base, leader);
-  return base + rank;
+  const LaneRun r = lane_run(valid, leaf);
+  if (valid && r.head) tally_add(c, smem, leaf, r.end - lane_id());
 }
 
 // ------------------------------------------------------------ phase: count1
@@ -598,71 +627,92 @@ __device__ __forceinline__ uint32_t warp_slot(const Ctx& c, bool valid, uint32_t
 __device__ void phase_count1(const Ctx& c, uint32_t* smem, uint32_t n_nodes, const int4* pts,
                              uint64_t n, unsigned long long base, uint64_t warp0,
                              uint64_t nwarps) {
+  constexpr int U = COUNT_U, D = DESCENT_GROUP;
   const NodeCache nc = load_node_cache(c, smem, n_nodes);
   WarpBuf wb = warp_buf(smem);
   const uint32_t lane = lane_id();
-  for (uint64_t w = warp0; w * 32 < n; w += nwarps) {
-    uint64_t i = w * 32 + lane;
-    bool valid = i < n;
-    int4 p = valid ? __ldcg(pts + i) : make_int4(0, 0, 0, 0);
-    uint32_t rx = 0, ry = 0, rz = 0;
-    if (valid && !rel_coords(c, p, rx, ry, rz)) {
-      atomicOr(&c.ctl->reject, 1u);
-      valid = false;
-    }
-    const uint32_t gidx = (uint32_t)(base + i);
-    uint32_t node = 0, L = c.rlog2;
-    bool walking = valid;
-    while (__any_sync(FULL_MASK, walking)) {
-      // Walk up to DESCENT_GROUP levels through the node table first and
-      // issue their grid-word loads together (their addresses do not depend
-      // on each other), then test the bits and claim level by level.
-      uint32_t gnode[DESCENT_GROUP], gcell[DESCENT_GROUP], gword[DESCENT_GROUP];
-      bool ginner[DESCENT_GROUP];
+  // each warp carries U units of 32 points (w, w + nwarps, ...) at a time so
+  // that their L2 round trips overlap
+  for (uint64_t w0 = warp0; w0 * 32 < n; w0 += U * nwarps) {
+    bool valid[U], walking[U];
+    int4 p[U];
+    uint32_t rx[U], ry[U], rz[U], node[U], L[U], gidx[U];
 #pragma unroll
-      for (int k = 0; k < DESCENT_GROUP; ++k) {
-        ginner[k] = false;
-        gnode[k] = node;
-        gcell[k] = 0;
-        gword[k] = 0;
-        if (walking) {
-          const uint32_t ch = node_child(c, nc, node);
-          if (ch == NONE) {
-            walking = false;
-          } else {
-            const uint32_t gref = node_grid(c, nc, node);
-            const uint32_t cell = cell_index(rx, ry, rz, L, c.G);
-            const uint32_t nxt = ch + octant(rx, ry, rz, L);
-            if (!ref_ok(c, gref, c.grid_bytes) || nxt >= c.max_nodes) {
-              set_error(c, E_INTERNAL);
-              walking = false;
+    for (int j = 0; j < U; ++j) {
+      const uint64_t i = (w0 + j * nwarps) * 32 + lane;
+      valid[j] = i < n;
+      p[j] = valid[j] ? __ldcg(pts + i) : make_int4(0, 0, 0, 0);
+      gidx[j] = (uint32_t)(base + i);
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      rx[j] = ry[j] = rz[j] = 0;
+      if (valid[j] && !rel_coords(c, p[j], rx[j], ry[j], rz[j])) {
+        atomicOr(&c.ctl->reject, 1u);
+        valid[j] = false;
+      }
+      node[j] = 0;
+      L[j] = c.rlog2;
+      walking[j] = valid[j];
+    }
+    for (;;) {
+      bool any = false;
+#pragma unroll
+      for (int j = 0; j < U; ++j) any = any || walking[j];
+      if (!__any_sync(FULL_MASK, any)) break;
+      // Walk up to D levels through the node table first and issue their
+      // grid-word loads together (their addresses do not depend on each
+      // other), then test the bits and claim all of them at once.
+      uint32_t gnode[U * D], gcell[U * D], gword[U * D];
+      bool ginner[U * D];
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const int s = j * D + k;
+          ginner[s] = false;
+          gnode[s] = node[j];
+          gcell[s] = 0;
+          gword[s] = 0;
+          if (walking[j]) {
+            const uint32_t ch = node_child(c, nc, node[j]);
+            if (ch == NONE) {
+              walking[j] = false;
             } else {
-              ginner[k] = true;
-              gcell[k] = cell;
-              gword[k] = grid_words(c, gref)[cell >> 5];
-              node = nxt;
-              --L;
+              const uint32_t gref = node_grid(c, nc, node[j]);
+              const uint32_t cell = cell_index(rx[j], ry[j], rz[j], L[j], c.G);
+              const uint32_t nxt = ch + octant(rx[j], ry[j], rz[j], L[j]);
+              if (!ref_ok(c, gref, c.grid_bytes) || nxt >= c.max_nodes) {
+                set_error(c, E_INTERNAL);
+                walking[j] = false;
+              } else {
+                ginner[s] = true;
+                gcell[s] = cell;
+                gword[s] = grid_words(c, gref)[cell >> 5];
+                node[j] = nxt;
+                --L[j];
+              }
             }
           }
         }
       }
-      bool want[DESCENT_GROUP];
-      unsigned long long key[DESCENT_GROUP];
+      bool want[U * D];
+      unsigned long long key[U * D];
+      uint32_t gg[U * D], gc[U * D];
 #pragma unroll
-      for (int k = 0; k < DESCENT_GROUP; ++k) {
-        want[k] = ginner[k] && ((gword[k] >> (gcell[k] & 31u)) & 1u) == 0u;
-        key[k] = ((unsigned long long)gnode[k] << (3u * c.G)) | gcell[k];
+      for (int s = 0; s < U * D; ++s) {
+        want[s] = ginner[s] && ((gword[s] >> (gcell[s] & 31u)) & 1u) == 0u;
+        key[s] = ((unsigned long long)gnode[s] << (3u * c.G)) | gcell[s];
+        gg[s] = gidx[s / D];
+        gc[s] = (uint32_t)p[s / D].w;
       }
-      uint32_t gg[DESCENT_GROUP], gc[DESCENT_GROUP];
-#pragma unroll
-      for (int k = 0; k < DESCENT_GROUP; ++k) {
-        gg[k] = gidx;
-        gc[k] = (uint32_t)p.w;
-      }
-      warp_claim<DESCENT_GROUP>(c, wb, want, key, gg, gc, gnode);
+      warp_claim<U * D, true>(c, wb, want, key, gg, gc, gnode);
     }
-    warp_tally(c, smem, valid, node);
-    if (valid) c.b_cur[i] = node;
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      warp_tally(c, smem, valid[j], node[j]);
+      if (valid[j]) c.b_cur[(w0 + j * nwarps) * 32 + lane] = node[j];
+    }
   }
   warp_flush(c, wb);
   tally_flush(c, smem);
@@ -694,7 +744,7 @@ __device__ __forceinline__ void advance_items(const Ctx& c, WarpBuf& wb, const b
     key[j] = ((unsigned long long)cur[j] << (3u * c.G)) | cell;
     rgba[j] = (uint32_t)p[j].w;
   }
-  warp_claim<U>(c, wb, moving, key, gidx, rgba, cur);
+  warp_claim<U, false>(c, wb, moving, key, gidx, rgba, cur);
 #pragma unroll
   for (int j = 0; j < U; ++j) {
     warp_tally(c, wb.smem, moving[j], nxt[j]);
@@ -1061,6 +1111,9 @@ __device__ __forceinline__ void warp_place(const Ctx& c, const bool (&valid)[U],
     map[j] = valid[j] ? *reinterpret_cast<const uint4*>(&c.meta[node[j]].st_nch)
                       : make_uint4(0, NONE, 0, 0);
   }
+  // exact groups here (a match over the warp): the cursor atomics return a
+  // value, and in dense regions the lanes of one node are not contiguous, so
+  // one reservation per lane run would queue many more of them on one counter
 #pragma unroll
   for (int j = 0; j < U; ++j) {
     const unsigned m = __ballot_sync(FULL_MASK, valid[j]);
