@@ -31,8 +31,10 @@
 // an update are listed (the backlog of Section 5.2) and cleared by store.
 //
 // Descents read the node table (first child, grid reference) from a copy in
-// shared memory of the first NODE_CACHE nodes, taken at the start of each
-// count / advance pass; the node ids of the upper levels are the smallest.
+// shared memory of the first NODE_CACHE nodes (the node ids of the upper
+// levels are the smallest): the plain form's count / advance kernels load it,
+// the persistent kernel loads it once and patches it after every decide
+// round with the nodes that split or were created.
 // Per-node counters are summed per block in shared memory before they reach
 // the global counters (the block tally cache).
 #pragma once
@@ -52,7 +54,7 @@ constexpr uint32_t REF_BYTES = 256;  // chunk, grid and directory references cou
 constexpr uint32_t CHUNK_HEADER = 16;
 // Launch-shape and algorithm knobs (compile-time; -D overrides them).
 #ifndef SL_NODE_CACHE
-#define SL_NODE_CACHE 8192
+#define SL_NODE_CACHE 4096
 #endif
 #ifndef SL_DESCENT_GROUP
 #define SL_DESCENT_GROUP 2
@@ -81,7 +83,10 @@ constexpr uint32_t WBUF = 64;                          // new-cell slots staged 
 constexpr int PHASE_BLOCK = SL_PHASE_BLOCK;            // threads of count / advance / fused blocks
 constexpr int PHASE_MIN_BLOCKS = SL_PHASE_MIN_BLOCKS;  // resident blocks per SM they aim for
 // dynamic shared memory of the count / advance / fused blocks
-constexpr uint32_t MVBUF = 128;                         // mover-list entries staged per warp
+#ifndef SL_MVBUF
+#define SL_MVBUF 128
+#endif
+constexpr uint32_t MVBUF = SL_MVBUF;                    // mover-list entries staged per warp
 constexpr uint32_t TALLY_LOG2 = 9;                      // block tally cache: 512 nodes
 constexpr uint32_t TALLY_SLOTS = 1u << TALLY_LOG2;
 // dynamic shared memory of the count / advance / fused blocks: node cache,
@@ -288,24 +293,49 @@ struct NodeCache {
   uint32_t n;  // cached nodes
 };
 
-// The whole block loads the cache and empties the block tally cache (call
-// after a grid/kernel boundary).
-__device__ __forceinline__ NodeCache load_node_cache(const Ctx& c, uint32_t* smem,
-                                                     uint32_t n_nodes) {
+// The cache of the first min(n_nodes, NODE_CACHE) nodes in `smem`.
+__device__ __forceinline__ NodeCache node_cache_at(uint32_t* smem, uint32_t n_nodes) {
   NodeCache nc;
   nc.child = smem;
   nc.grid = smem + NODE_CACHE;
   nc.n = n_nodes < NODE_CACHE ? n_nodes : NODE_CACHE;
-  for (uint32_t i = threadIdx.x; i < nc.n; i += blockDim.x) {
-    nc.child[i] = c.child[i];
-    nc.grid[i] = c.gridref[i];
+  return nc;
+}
+
+// The whole block copies nodes [lo, hi) (those below NODE_CACHE) into the
+// cache. The caller synchronises the block before the cache is read.
+__device__ __forceinline__ void node_cache_load(const Ctx& c, uint32_t* smem, uint32_t lo,
+                                                uint32_t hi) {
+  hi = hi < NODE_CACHE ? hi : NODE_CACHE;
+  for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    smem[i] = c.child[i];
+    smem[NODE_CACHE + i] = c.gridref[i];
   }
+}
+
+// The whole block brings the cache up to date after a decide round: the
+// nodes of the split entries [s_lo, s_hi) became inner (child and grid set),
+// the nodes [n_lo, n_hi) were created (leaves without a grid). Nothing else
+// in the node table changes during an update. The caller synchronises.
+__device__ __forceinline__ void node_cache_patch(const Ctx& c, uint32_t* smem, uint32_t s_lo,
+                                                 uint32_t s_hi, uint32_t n_lo, uint32_t n_hi) {
+  for (uint32_t e = s_lo + threadIdx.x; e < s_hi; e += blockDim.x) {
+    const uint32_t id = c.splits[e].node;
+    if (id < NODE_CACHE) {
+      smem[id] = c.child[id];
+      smem[NODE_CACHE + id] = c.gridref[id];
+    }
+  }
+  node_cache_load(c, smem, n_lo, n_hi);
+}
+
+// The whole block empties the block tally cache (at the start of a phase,
+// before a block barrier).
+__device__ __forceinline__ void tally_init(uint32_t* smem) {
   for (uint32_t i = threadIdx.x; i < TALLY_SLOTS; i += blockDim.x) {
     smem[SMEM_TALLY + i] = NONE;
     smem[SMEM_TALLY + TALLY_SLOTS + i] = 0;
   }
-  __syncthreads();
-  return nc;
 }
 
 // ------------------------------------------------------ block tally cache
@@ -624,11 +654,12 @@ __device__ __forceinline__ void warp_tally(const Ctx& c, uint32_t* smem, bool va
 
 // Iteration 1 for the batch points [0, n): descend, claim, count. `smem`
 // holds PHASE_SMEM_BYTES of dynamic shared memory; n_nodes is the node count.
-__device__ void phase_count1(const Ctx& c, uint32_t* smem, uint32_t n_nodes, const int4* pts,
+__device__ void phase_count1(const Ctx& c, uint32_t* smem, const NodeCache nc, const int4* pts,
                              uint64_t n, unsigned long long base, uint64_t warp0,
                              uint64_t nwarps) {
   constexpr int U = COUNT_U, D = DESCENT_GROUP;
-  const NodeCache nc = load_node_cache(c, smem, n_nodes);
+  tally_init(smem);
+  __syncthreads();  // also publishes the caller's node-cache writes
   WarpBuf wb = warp_buf(smem);
   const uint32_t lane = lane_id();
   // each warp carries U units of 32 points (w, w + nwarps, ...) at a time so
@@ -771,11 +802,12 @@ constexpr uint32_t MV_SPILL = 1u << 31;
 // rounds only the n_in entries of mover list in_list, which carry cursor and
 // level. Points are cut into 32-item warp units (a unit of a task never
 // crosses into the next task).
-__device__ void phase_advance(const Ctx& c, uint32_t* smem, uint32_t n_nodes, const int4* pts,
+__device__ void phase_advance(const Ctx& c, uint32_t* smem, const NodeCache nc, const int4* pts,
                               uint64_t n, unsigned long long base, uint32_t t_hi, uint32_t s_lo,
                               uint32_t s_hi, int in_list, uint32_t n_in, int out_list,
                               uint64_t warp0, uint64_t nwarps) {
-  const NodeCache nc = load_node_cache(c, smem, n_nodes);
+  tally_init(smem);
+  __syncthreads();  // also publishes the caller's node-cache writes
   WarpBuf wb = warp_buf(smem);
   MoverBuf mb = mover_buf(smem);
   const uint32_t lane = lane_id();

@@ -127,6 +127,8 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
   extern __shared__ uint32_t smem[];  // node-table cache (PHASE_SMEM_BYTES)
   PhaseClock clk{t_begin};
   const uint32_t nb = n_dev ? min(vload(n_dev), n_batches) : n_batches;
+  // the node-table cache is loaded once and patched after every decide round
+  node_cache_load(c, smem, 0, vload(&c.ctl->n_nodes));
   for (uint32_t b = 0; b < nb; ++b) {
     // every value read here was written before the last barrier and is not
     // written again before the next one, so all threads decide alike
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
       bd.pts = c.staging;
     }
     if (bd.n) {
-      phase_count1(c, smem, nodes0, bd.pts, bd.n, base, warp0, nwarps);
+      phase_count1(c, smem, node_cache_at(smem, nodes0), bd.pts, bd.n, base, warp0, nwarps);
       if (!grid_barrier(c, f)) return;
       clk.tick(c, PH_COUNT);
       rejected = vload(&c.ctl->reject) != 0u;  // set only by the count round
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
           clk.tick(c, PH_DECIDE);
           const uint32_t sc = vload(&c.ctl->split_count), nn = vload(&c.ctl->n_nodes);
           const uint32_t nt = vload(&c.ctl->ntasks);
+          node_cache_patch(c, smem, s_hi, sc, n_hi, nn);  // this round's splits and new nodes
           if (iters == 1) t_hi = nt;
           else if (nt != t_hi && tid == 0) set_error(c, E_INTERNAL);
           if (sc == s_hi) break;
@@ -188,8 +191,8 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
           n_hi = nn;
           const int in_list = iters >= 2 ? (int)((iters - 2) & 1u) : -1;
           const uint32_t n_in = in_list >= 0 ? vload(&c.ctl->mv_count[in_list]) : 0u;
-          phase_advance(c, smem, nn, bd.pts, bd.n, base, t_hi, s_lo, s_hi, in_list, n_in,
-                        (int)((iters - 1) & 1u), warp0, nwarps);
+          phase_advance(c, smem, node_cache_at(smem, nn), bd.pts, bd.n, base, t_hi, s_lo, s_hi,
+                        in_list, n_in, (int)((iters - 1) & 1u), warp0, nwarps);
           ++iters;
           if (!grid_barrier(c, f)) return;
           clk.tick(c, PH_ADVANCE);

@@ -60,7 +60,9 @@ __global__ void __launch_bounds__(PBLOCK, PHASE_MIN_BLOCKS) k_count1(Ctx c, cons
                                                     unsigned long long base, uint32_t n_nodes) {
   extern __shared__ uint32_t smem[];
   const uint64_t warps_per_block = blockDim.x / 32;
-  phase_count1(c, smem, n_nodes, pts, n, base, blockIdx.x * warps_per_block + threadIdx.x / 32,
+  node_cache_load(c, smem, 0, n_nodes);
+  phase_count1(c, smem, node_cache_at(smem, n_nodes), pts, n, base,
+               blockIdx.x * warps_per_block + threadIdx.x / 32,
                (uint64_t)gridDim.x * warps_per_block);
 }
 
@@ -83,7 +85,9 @@ __global__ void __launch_bounds__(PBLOCK, PHASE_MIN_BLOCKS) k_advance(Ctx c, con
                                                      int in_list, uint32_t n_in, int out_list) {
   extern __shared__ uint32_t smem[];
   const uint64_t warps_per_block = blockDim.x / 32;
-  phase_advance(c, smem, n_nodes, pts, n, base, t_hi, s_lo, s_hi, in_list, n_in, out_list,
+  node_cache_load(c, smem, 0, n_nodes);
+  phase_advance(c, smem, node_cache_at(smem, n_nodes), pts, n, base, t_hi, s_lo, s_hi, in_list,
+                n_in, out_list,
                 blockIdx.x * warps_per_block + threadIdx.x / 32,
                 (uint64_t)gridDim.x * warps_per_block);
 }
