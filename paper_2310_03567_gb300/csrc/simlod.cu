@@ -607,6 +607,13 @@ SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t are
     delete h;
     return SIMLOD_ERR_CUDA;
   }
+#ifdef SL_CARVEOUT
+  // shared-memory share of the unified L1/shared storage, in percent
+  cudaFuncSetAttribute(k_fused, cudaFuncAttributePreferredSharedMemoryCarveout, SL_CARVEOUT);
+  cudaFuncSetAttribute(k_count1, cudaFuncAttributePreferredSharedMemoryCarveout, SL_CARVEOUT);
+  cudaFuncSetAttribute(k_advance, cudaFuncAttributePreferredSharedMemoryCarveout, SL_CARVEOUT);
+  cudaGetLastError();
+#endif
   int coop = 0, bpsm = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_fused, FUSED_BLOCK,
