@@ -71,6 +71,9 @@ constexpr uint32_t CHUNK_HEADER = 16;
 #ifndef SL_STORE_UNROLL
 #define SL_STORE_UNROLL 2
 #endif
+#ifndef SL_STORE_BLOCK
+#define SL_STORE_BLOCK 1
+#endif
 #ifndef SL_BLOCK_TALLY
 #define SL_BLOCK_TALLY 1
 #endif
@@ -1185,6 +1188,95 @@ __device__ __forceinline__ void warp_place(const Ctx& c, const bool (&valid)[U],
   }
 }
 
+// Block form of warp_place (all threads of the block call; loops are
+// block-uniform): items of the whole block reserve their slots per node in a
+// shared-memory table first (256 slots, direct-mapped, in the tally region),
+// then one thread per table entry takes the node's range with one global
+// atomicAdd. In dense regions many warps of a block store into the same few
+// nodes; their returning atomics on one counter would queue at one L2 slice.
+// Items whose table slot holds another node take the warp path.
+constexpr uint32_t PLACE_SLOTS = 256;
+
+template <int U>
+__device__ __forceinline__ void block_place(const Ctx& c, uint32_t* smem, const bool (&valid)[U],
+                                            const uint32_t (&node)[U], uint32_t (&ref)[U],
+                                            uint32_t (&q)[U]) {
+  const uint32_t lane = lane_id();
+  uint32_t* tn = smem + SMEM_TALLY;  // node of each table slot
+  uint32_t* tc = tn + PLACE_SLOTS;   // items of the block for it
+  uint32_t* tb = tc + PLACE_SLOTS;   // the range it got
+  uint4 map[U];
+  uint32_t sl[U], rank[U], cur[U];
+  int leader[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    map[j] = valid[j] ? *reinterpret_cast<const uint4*>(&c.meta[node[j]].st_nch)
+                      : make_uint4(0, NONE, 0, 0);
+    sl[j] = NONE;
+    rank[j] = 0;
+    if (valid[j]) {
+      const uint32_t h = (node[j] * 0x9E3779B1u) >> 24;  // PLACE_SLOTS = 2^8
+      const uint32_t old = tn[h] == node[j] ? node[j] : atomicCAS(tn + h, NONE, node[j]);
+      if (old == NONE || old == node[j]) {
+        sl[j] = h;
+        rank[j] = atomicAdd(tc + h, 1u);
+      }
+    }
+  }
+  // items without a table slot: exact groups of the warp, one global atomic each
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const bool fb = valid[j] && sl[j] == NONE;
+    const unsigned m = __ballot_sync(FULL_MASK, fb);
+    leader[j] = 0;
+    cur[j] = 0;
+    if (fb) {
+      const unsigned grp = __match_any_sync(m, node[j]);
+      leader[j] = __ffs(grp) - 1;
+      rank[j] = __popc(grp & ((1u << lane) - 1u));
+      if ((int)lane == leader[j]) cur[j] = atomicAdd(&c.scur[node[j]], (uint32_t)__popc(grp));
+    }
+    cur[j] = __shfl_sync(FULL_MASK, cur[j], leader[j]);
+  }
+  __syncthreads();
+  for (uint32_t t = threadIdx.x; t < PLACE_SLOTS; t += blockDim.x) {
+    const uint32_t nd = tn[t];
+    if (nd != NONE) tb[t] = atomicAdd(&c.scur[nd], tc[t]);
+    tn[t] = NONE;  // every thread has passed its table lookups (barrier above)
+    tc[t] = 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    ref[j] = NONE;
+    q[j] = 0;
+    if (valid[j]) {
+      const uint32_t slot = map[j].w + (sl[j] != NONE ? tb[sl[j]] : cur[j]) + rank[j];
+      const uint32_t k = slot / c.C;
+      q[j] = slot - k * c.C;
+      if (k + 1u == map[j].x) {
+        ref[j] = map[j].y;
+      } else if (k >= map[j].x) {
+        const unsigned long long at = (unsigned long long)map[j].z + (k - map[j].x);
+        if (at < c.max_chunks) ref[j] = c.alloc_refs[at];
+      }
+      if (!ref_ok(c, ref[j], c.chunk_bytes)) {
+        set_error(c, E_INTERNAL);
+        ref[j] = NONE;
+      }
+    }
+  }
+}
+
+// All threads of the block call: an empty block placement table.
+__device__ __forceinline__ void block_place_init(uint32_t* smem) {
+  for (uint32_t t = threadIdx.x; t < PLACE_SLOTS; t += blockDim.x) {
+    smem[SMEM_TALLY + t] = NONE;
+    smem[SMEM_TALLY + PLACE_SLOTS + t] = 0;
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ void put_rec(const Ctx& c, uint32_t ref, uint32_t q, int4 rec,
                                         uint32_t aux) {
   if (ref == NONE) return;
@@ -1193,6 +1285,7 @@ __device__ __forceinline__ void put_rec(const Ctx& c, uint32_t ref, uint32_t q, 
 }
 
 constexpr int STORE_U = SL_STORE_UNROLL;
+static_assert(3 * 256 <= 2 * TALLY_SLOTS, "the block placement table fits the tally region");
 
 // Store the batch points, the n_spill re-inserted points (from the spill
 // records) and the n_keys new voxels, each at the next free slot of its node;
@@ -1200,19 +1293,34 @@ constexpr int STORE_U = SL_STORE_UNROLL;
 // pool_top (the caller then raises pool_top). Loops are warp-uniform so that the
 // lanes of a warp share one slot reservation per node; each lane carries
 // STORE_U items at a time so that their L2 round trips overlap.
-__device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned long long base,
-                            uint32_t n_spill, uint32_t n_tasks, uint32_t n_keys, int pool_top,
-                            uint64_t t0, uint64_t nthreads) {
+__device__ void phase_store(const Ctx& c, uint32_t* smem, const int4* pts, uint64_t n,
+                            unsigned long long base, uint32_t n_spill, uint32_t n_tasks,
+                            uint32_t n_keys, int pool_top, uint64_t t0, uint64_t nthreads) {
   constexpr int U = STORE_U;
   const uint32_t lane = lane_id();
-  const uint64_t w0 = t0 - lane, wstride = nthreads;  // warp-aligned start and stride
-  for (uint64_t b0 = w0; b0 < n; b0 += U * wstride) {
+  // block-uniform loops: item j of thread t in round b is b + j * nthreads + t
+  const uint64_t blk = t0 - threadIdx.x, stride = nthreads;
+  const uint64_t me = threadIdx.x;
+  auto place = [&](const bool (&valid)[U], const uint32_t (&node)[U], uint32_t (&ref)[U],
+                   uint32_t (&q)[U]) {
+#if SL_STORE_BLOCK
+    if (smem) {
+      block_place<U>(c, smem, valid, node, ref, q);
+      return;
+    }
+#endif
+    warp_place<U>(c, valid, node, ref, q);
+  };
+#if SL_STORE_BLOCK
+  if (smem) block_place_init(smem);
+#endif
+  for (uint64_t b0 = blk; b0 < n; b0 += U * stride) {
     bool valid[U];
     uint32_t node[U], ref[U], q[U];
     int4 p[U];
 #pragma unroll
     for (int j = 0; j < U; ++j) {
-      const uint64_t i = b0 + j * wstride + lane;
+      const uint64_t i = b0 + j * stride + me;
       valid[j] = i < n;
       node[j] = valid[j] ? c.b_cur[i] : 0u;
       p[j] = valid[j] ? __ldcg(pts + i) : make_int4(0, 0, 0, 0);
@@ -1221,17 +1329,17 @@ __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned 
         valid[j] = false;
       }
     }
-    warp_place<U>(c, valid, node, ref, q);
+    place(valid, node, ref, q);
 #pragma unroll
-    for (int j = 0; j < U; ++j) put_rec(c, ref[j], q[j], p[j], (uint32_t)(base + b0 + j * wstride + lane));
+    for (int j = 0; j < U; ++j) put_rec(c, ref[j], q[j], p[j], (uint32_t)(base + b0 + j * stride + me));
   }
-  for (uint64_t b0 = w0; b0 < n_spill; b0 += U * wstride) {
+  for (uint64_t b0 = blk; b0 < n_spill; b0 += U * stride) {
     bool valid[U];
     uint32_t node[U], ref[U], q[U], g[U];
     int4 r[U];
 #pragma unroll
     for (int j = 0; j < U; ++j) {
-      const uint64_t e = b0 + j * wstride + lane;
+      const uint64_t e = b0 + j * stride + me;
       valid[j] = e < n_spill;
       node[j] = valid[j] ? c.sp_cur[e] : 0u;
       r[j] = valid[j] ? c.sp_rec[e] : make_int4(0, 0, 0, 0);
@@ -1241,18 +1349,18 @@ __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned 
         valid[j] = false;
       }
     }
-    warp_place<U>(c, valid, node, ref, q);
+    place(valid, node, ref, q);
 #pragma unroll
     for (int j = 0; j < U; ++j) put_rec(c, ref[j], q[j], r[j], g[j]);
   }
   const uint32_t G = c.G, cmask = (1u << (3u * G)) - 1u, amask = (1u << G) - 1u;
-  for (uint64_t b0 = w0; b0 < n_keys; b0 += U * wstride) {
+  for (uint64_t b0 = blk; b0 < n_keys; b0 += U * stride) {
     bool valid[U];
     uint32_t node[U], ref[U], q[U], cell[U], gref[U], rgba[U];
     HSlot* sl[U];
 #pragma unroll
     for (int j = 0; j < U; ++j) {
-      const uint64_t e = b0 + j * wstride + lane;
+      const uint64_t e = b0 + j * stride + me;
       valid[j] = e < n_keys;
       sl[j] = valid[j] ? c.hash + c.keys[e] : nullptr;
     }
@@ -1270,7 +1378,7 @@ __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned 
       if (valid[j] && !ok) set_error(c, E_INTERNAL);
       valid[j] = ok;
     }
-    warp_place<U>(c, valid, node, ref, q);
+    place(valid, node, ref, q);
 #pragma unroll
     for (int j = 0; j < U; ++j) {
       if (!valid[j]) continue;
@@ -1289,6 +1397,7 @@ __device__ void phase_store(const Ctx& c, const int4* pts, uint64_t n, unsigned 
       sl[j]->val = HASH_EMPTY;
     }
   }
+  (void)lane;
   const int top = pool_top > 0 ? pool_top : 0;
   if ((unsigned long long)top + n_tasks > c.max_chunks) {
     if (t0 == 0) set_error(c, E_POOL);

@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
         const uint32_t n_spill = min(vload(&c.ctl->spill_count), c.spill_cap);
         const uint32_t n_keys = min(vload(&c.ctl->nkeys), c.backlog_cap);
         const int pool_top = vload(&c.ctl->pool_top);
-        phase_store(c, bd.pts, bd.n, base, n_spill, n_tasks, n_keys, pool_top, tid, nthreads);
+        phase_store(c, smem, bd.pts, bd.n, base, n_spill, n_tasks, n_keys, pool_top, tid,
+                    nthreads);
         if (!grid_barrier(c, f)) return;
         clk.tick(c, PH_STORE);
         if (tid == 0) phase_end(c, bd.n, iters);

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(PBLOCK, PHASE_MIN_BLOCKS) k_advance(Ctx c, con
 __global__ void __launch_bounds__(BLOCK) k_store(Ctx c, const int4* pts, uint64_t n,
                                                   unsigned long long base, uint32_t n_spill,
                                                   uint32_t n_tasks, uint32_t n_keys, int pool_top) {
-  phase_store(c, pts, n, base, n_spill, n_tasks, n_keys, pool_top,
+  phase_store(c, nullptr, pts, n, base, n_spill, n_tasks, n_keys, pool_top,
               blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
 
