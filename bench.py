@@ -212,12 +212,14 @@ def make_octree(w, root_log2: int, chunk_points: int = 1000):
 
     from paper_2310_03567_gb300 import simlod
     max_batch = int(max(w.counts))
-    # claim table: 2 slots per backlog entry; up to 2 new voxels per batch
-    # point keeps the table (64 MB for 1M-point batches) mostly L2-resident
+    # claim table: 2 slots per backlog entry. Up to 2 new voxels per batch
+    # point, but at most 8M per update (these workloads make under 5M new
+    # voxels in any one update): the table (64-256 MB) stays mostly
+    # L2-resident instead of a 1 GB table for 10M-point batches
     cfg = simlod.default_config(root_min=w.root_min, root_log2=root_log2,
                                 max_batch_points=max_batch,
                                 spill_capacity=max(8 << 20, 2 * max_batch),
-                                backlog_capacity=max(2 << 20, 2 * max_batch),
+                                backlog_capacity=max(2 << 20, min(2 * max_batch, 8 << 20)),
                                 max_nodes=1 << 21, chunk_points=chunk_points)
     # plus the part-filled last chunk of up to 64k nodes
     data_bytes = max(256 << 20, w.n_points * 80) + (1 << 16) * 20 * chunk_points
