@@ -82,7 +82,10 @@ constexpr uint32_t NODE_CACHE_BYTES = NODE_CACHE * 8;  // child + grid reference
 constexpr uint32_t ZERO_UNIT = 4096;                   // bytes of grid zeroed per warp unit
 constexpr int DESCENT_GROUP = SL_DESCENT_GROUP;        // levels whose grid words load together
 constexpr int COUNT_U = SL_COUNT_UNROLL;               // count units a warp carries at a time
-constexpr uint32_t WBUF = 64;                          // new-cell slots staged per warp
+#ifndef SL_WBUF
+#define SL_WBUF 128
+#endif
+constexpr uint32_t WBUF = SL_WBUF;                      // new-cell slots staged per warp
 constexpr int PHASE_BLOCK = SL_PHASE_BLOCK;            // threads of count / advance / fused blocks
 constexpr int PHASE_MIN_BLOCKS = SL_PHASE_MIN_BLOCKS;  // resident blocks per SM they aim for
 // dynamic shared memory of the count / advance / fused blocks
