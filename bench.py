@@ -205,13 +205,14 @@ def run_reference(args):
     return 0
 
 
-def make_octree(w, root_log2: int, chunk_points: int = 1000):
+def make_octree(w, root_log2: int, chunk_points: int = 1000, max_batch: int | None = None):
     """The octree the bench times for workload w (its capacities follow the
-    workload's largest batch); the full-size tests build the same one."""
+    workload's largest batch, or max_batch: the batched form merges batches
+    into updates of up to that size); the full-size tests build the same one."""
     import torch
 
     from paper_2310_03567_gb300 import simlod
-    max_batch = int(max(w.counts))
+    max_batch = max(int(max(w.counts)), int(max_batch or 0))
     # claim table: 2 slots per backlog entry. Up to 2 new voxels per batch
     # point, but at most 8M per update (these workloads make under 5M new
     # voxels in any one update): the table (64-256 MB) stays mostly
@@ -288,7 +289,7 @@ def run_ours(args):
     ptrs = [dev_pts.data_ptr() + int(o) * 16 for o in w.offsets]
     counts = [int(c) for c in w.counts]
     max_batch = max(counts)
-    tree = make_octree(w, root_log2)
+    tree = make_octree(w, root_log2, max_batch=args.max_batch)
     cfg = tree.cfg
     stream = tree.stream
 
@@ -754,6 +755,9 @@ def main():
                     help="chunk-size study instead of the standard measurement")
     ap.add_argument("--morton", action="store_true",
                     help="sort the workload's stream in Morton order before cutting it")
+    ap.add_argument("--max-batch", type=int, default=None,
+                    help="octree batch capacity (staging) above the workload's largest batch: "
+                         "lets the batched form merge small batches into larger updates")
     ap.add_argument("--batched", action="store_true",
                     help="also time the batched form (always on for --workload mixed)")
     args = ap.parse_args()
