@@ -210,7 +210,12 @@ struct Ctx {
   uint32_t max_nodes, max_chunks, spill_cap, backlog_cap, max_splits;
   uint64_t max_batch;
   uint64_t mv_cap;  // entries of each mover list (batch + spill capacity)
+  unsigned long long* launch_bar;  // barrier word of the persistent launch (abort bit)
 };
+
+// Abort bit of a persistent launch's barrier word: set with the first
+// device error, so that every block leaves at its next barrier.
+constexpr unsigned long long BAR_ABORT = 1ull << 63;
 
 // ------------------------------------------------------------------ helpers
 
@@ -227,6 +232,7 @@ __device__ __forceinline__ unsigned long long fmix64(unsigned long long k) {
 
 __device__ __forceinline__ void set_error(const Ctx& c, uint32_t bits) {
   atomicOr(&c.ctl->error, bits);
+  atomicOr(c.launch_bar, BAR_ABORT);
 }
 
 __device__ __forceinline__ uint8_t* ref_ptr(const Ctx& c, uint32_t ref) {

@@ -37,13 +37,13 @@ struct PlanSeg {
 
 // Per-launch control words of the fused kernel (arena).
 struct FusedCtl {
-  unsigned int bar_count;
-  unsigned int bar_gen;
-  unsigned int abort;
+  // block arrivals at grid barriers since the launch began (gridDim.x per
+  // barrier); bit 63 (BAR_ABORT) aborts the launch
+  unsigned long long bar;
   unsigned int consumed;  // batches fully handled (applied or rejected)
   unsigned int stop;      // the frame budget ran out
   unsigned int rejected;  // batches rejected in this launch
-  unsigned int pad[10];
+  unsigned int pad[11];
 };
 static_assert(sizeof(FusedCtl) == 64, "FusedCtl size");
 
@@ -53,41 +53,48 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// Grid-wide barrier with a time limit. Returns false when the launch was
-// aborted (by this block's timeout or another's).
+// Grid-wide barrier with a time limit. Thread 0 of each block publishes the
+// block's writes (fence, then one atomic add on the launch's arrival count)
+// and waits until the count reaches the end of this barrier's generation;
+// the last block to arrive waits for nothing. A device error sets the abort
+// bit of the same word (set_error), so a waiting block sees it in the value
+// it polls and an arriving block in the value its add returns: every block
+// leaves at its next barrier, and all blocks that run a phase have seen the
+// previous phase complete. Returns false when the launch was aborted.
 __device__ __forceinline__ bool grid_barrier(const Ctx& c, FusedCtl* f) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned int gen = vload(&f->bar_gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&f->bar_count, 1u);
-    int ok = 1;
-    if (arrived == gridDim.x - 1u) {
-      // every block has arrived: a device error raised before this barrier
-      // becomes one abort decision that all blocks read after it
-      if (vload(&c.ctl->error)) atomicExch(&f->abort, 1u);
-      atomicExch(&f->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&f->bar_gen, 1u);
-    } else {
+    unsigned long long* w = &f->bar;
+    unsigned long long v;
+    asm volatile(
+        "fence.acq_rel.gpu;\n\t"
+        "atom.relaxed.gpu.global.add.u64 %0, [%1], 1;"
+        : "=l"(v)
+        : "l"(w)
+        : "memory");
+    const unsigned long long g = gridDim.x;
+    const unsigned long long target = ((v & ~BAR_ABORT) / g + 1ull) * g;
+    int ok = (v & BAR_ABORT) == 0ull;
+    if (ok && (v & ~BAR_ABORT) + 1ull < target) {
       const unsigned long long t0 = globaltimer_ns();
-      while (vload(&f->bar_gen) == gen) {
-        if (vload(&f->abort)) {
+      for (uint32_t k = 1;; ++k) {
+        asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(w) : "memory");
+        if (v & BAR_ABORT) {
           ok = 0;
           break;
         }
-        if (globaltimer_ns() - t0 > FUSED_BARRIER_NS) {
-          atomicExch(&f->abort, 1u);
-          set_error(c, E_TIMEOUT);
+        if (v >= target) break;
+        if ((k & 15u) == 0u && globaltimer_ns() - t0 > FUSED_BARRIER_NS) {
+          set_error(c, E_TIMEOUT);  // also sets the abort bit
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
-    __threadfence();
-    s_ok = ok && !vload(&f->abort);
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;

@@ -258,6 +258,7 @@ void make_ctx(simlod_t* h) {
   uint8_t* a = h->arena;
   c.ctl = reinterpret_cast<Ctl*>(a + L.ctl);
   h->fctl_dev = reinterpret_cast<FusedCtl*>(a + L.fctl);
+  c.launch_bar = &h->fctl_dev->bar;
   h->batches_dev = reinterpret_cast<BatchDesc*>(a + L.batches);
   c.child = reinterpret_cast<uint32_t*>(a + L.child);
   c.gridref = reinterpret_cast<uint32_t*>(a + L.gridref);
