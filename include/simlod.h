@@ -205,6 +205,26 @@ SIMLOD_API int simlod_insert_batch_host(simlod_t* h, const simlod_point* h_pts, 
 SIMLOD_API int simlod_insert_batches(simlod_t* h, const simlod_point* const* d_batches,
                                      const uint64_t* counts, uint32_t n_batches, void* stream);
 
+/* Fused form fed from page-locked host memory (the host ingest pipeline;
+ * Section 4: the update kernel loops over the batches uploaded so far).
+ * Batch k is copied from h_batches[k] (page-locked host memory) to d_dst,
+ * the batches packed in order (d_dst: device memory, 16-byte aligned, room
+ * for the sum of counts), on copy_stream, and a 4-byte copy then sets
+ * d_ready[k] (n_batches words of device memory, cleared on `stream` first).
+ * One persistent launch on `stream` applies the batches in order, as
+ * simlod_insert_batches does, and starts batch k once d_ready[k] is set, so
+ * each copy overlaps the updates of the batches before it. copy_stream must
+ * not wait for work enqueued on `stream` after this call: a flag that stays
+ * clear for 2 s aborts the launch (simlod_sync then returns
+ * SIMLOD_ERR_TIMEOUT and the handle is poisoned). copy_stream may equal
+ * `stream` (no overlap). h_batches, d_dst and d_ready must stay valid until
+ * `stream` passes the launch. Rejections and errors as in
+ * simlod_insert_batches. */
+SIMLOD_API int simlod_insert_batches_host(simlod_t* h, const simlod_point* const* h_batches,
+                                          const uint64_t* counts, uint32_t n_batches,
+                                          simlod_point* d_dst, uint32_t* d_ready, void* stream,
+                                          void* copy_stream);
+
 /* Batched form: a plan for a fixed list of uneven batches (device pointers,
  * 16-byte aligned, at most 16,384), run as one CUDA graph (when capture is
  * possible, else as direct launches) of three kernels: a check of every batch

@@ -16,6 +16,7 @@
 namespace sl {
 
 constexpr unsigned long long FUSED_BARRIER_NS = 2000000000ull;  // 2 s
+constexpr unsigned long long FUSED_READY_NS = 2000000000ull;    // 2 s per batch
 constexpr int FUSED_BLOCK = PHASE_BLOCK;
 constexpr unsigned long long NO_BUDGET = ~0ull;
 constexpr uint32_t MAX_FUSED_BATCHES = 16384;
@@ -100,6 +101,40 @@ __device__ __forceinline__ bool grid_barrier(const Ctx& c, FusedCtl* f) {
   return s_ok != 0;
 }
 
+// Wait until a batch is ready: *flag != 0, written by a copy on another
+// stream after the batch's own copy (Section 4: the update kernel handles the
+// batches uploaded so far). Thread 0 of each block polls, bounded by
+// FUSED_READY_NS; the abort bit ends the wait too. Returns false when the
+// launch was aborted.
+__device__ __forceinline__ bool wait_ready(const Ctx& c, FusedCtl* f, const unsigned int* flag) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+    if (v == 0u) {
+      const unsigned long long t0 = globaltimer_ns();
+      for (uint32_t k = 1;; ++k) {
+        __nanosleep(128);
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v != 0u) break;
+        if (vload(&f->bar) & BAR_ABORT) {
+          ok = 0;
+          break;
+        }
+        if ((k & 15u) == 0u && globaltimer_ns() - t0 > FUSED_READY_NS) {
+          set_error(c, E_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // Phase clock (block 0, thread 0): charge the time since the previous tick
 // to `phase`. Called right after a barrier, so it covers the phase and the
 // barrier that closed it.
@@ -121,12 +156,16 @@ struct PhaseClock {
 //
 // n_dev != nullptr: the number of updates is read from the device (written by
 // the planning kernel before this launch) instead of n_batches.
+//
+// ready != nullptr: update b starts once ready[b] != 0 (its points were copied
+// by another stream, which then set the flag).
 __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, const BatchDesc* batches,
                                                         uint32_t n_batches, FusedCtl* f,
                                                         unsigned long long budget_ns,
                                                         uint32_t max_iters,
                                                         const unsigned int* n_dev,
-                                                        const PlanSeg* segs) {
+                                                        const PlanSeg* segs,
+                                                        const unsigned int* ready) {
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t warp0 = tid / 32, nwarps = nthreads / 32;
@@ -140,6 +179,7 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
     // every value read here was written before the last barrier and is not
     // written again before the next one, so all threads decide alike
     if (vload(&f->stop)) return;
+    if (ready && !wait_ready(c, f, ready + b)) return;
     BatchDesc bd = batches[b];
     const unsigned long long base = vload(&c.ctl->base);
     const uint32_t nodes0 = vload(&c.ctl->n_nodes);

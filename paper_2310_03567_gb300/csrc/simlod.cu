@@ -137,6 +137,8 @@ struct simlod {
   BatchDesc* desc_host;     // pinned staging of the batch table
   cudaEvent_t desc_done;    // the last batch-table copy has finished
   FusedCtl* fctl_host;      // pinned mirror of the fused control words
+  uint32_t* one_host;       // pinned word holding 1: the source of ready-flag copies
+  cudaEvent_t flags_clear;  // the ready flags of the last host-fed launch are cleared
   FusedCtl* fctl_dev;
   BatchDesc* batches_dev;
   // timing
@@ -470,7 +472,8 @@ int insert_device(simlod_t* h, const int4* pts, uint64_t n, cudaStream_t s) {
 
 // Enqueue one fused launch over n batches (device pointers + counts).
 int launch_fused(simlod_t* h, const simlod_point* const* d_batches, const uint64_t* counts,
-                 uint32_t n, unsigned long long budget_ns, cudaStream_t s) {
+                 uint32_t n, unsigned long long budget_ns, cudaStream_t s,
+                 const unsigned int* ready = nullptr) {
   if (h->fused_grid < 1) return SIMLOD_ERR_CUDA;
   uint64_t total = 0;
   for (uint32_t k = 0; k < n; ++k) {
@@ -496,7 +499,7 @@ int launch_fused(simlod_t* h, const simlod_point* const* d_batches, const uint64
   uint32_t max_iters = h->cfg.max_expand_iters ? h->cfg.max_expand_iters : h->cfg.root_log2 + 1;
   const unsigned int* n_dev = nullptr;
   const PlanSeg* segs = nullptr;
-  void* args[] = {&c, &bt, &n, &f, &budget_ns, &max_iters, &n_dev, &segs};
+  void* args[] = {&c, &bt, &n, &f, &budget_ns, &max_iters, &n_dev, &segs, &ready};
   cudaError_t le = cudaSuccess;
   int rc = launch(h, K_FUSED, s, [&] {
     le = cudaLaunchCooperativeKernel((const void*)k_fused, dim3(h->fused_grid),
@@ -626,10 +629,13 @@ SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t are
   if (cudaMallocHost(reinterpret_cast<void**>(&h->desc_host),
                      sizeof(BatchDesc) * MAX_FUSED_BATCHES) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&h->fctl_host), sizeof(FusedCtl)) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->desc_done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaMallocHost(reinterpret_cast<void**>(&h->one_host), sizeof(uint32_t)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->desc_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->flags_clear, cudaEventDisableTiming) != cudaSuccess) {
     simlod_destroy(h);
     return SIMLOD_ERR_CUDA;
   }
+  *h->one_host = 1u;
   // the arena is the caller's memory: start from a zeroed control block
   if (cudaMemsetAsync(h->ctx.ctl, 0, sizeof(Ctl), static_cast<cudaStream_t>(stream)) !=
       cudaSuccess) {
@@ -679,6 +685,47 @@ SIMLOD_API int simlod_insert_batches(simlod_t* h, const simlod_point* const* d_b
   if (n_batches == 0) return SIMLOD_OK;
   return launch_fused(h, d_batches, counts, n_batches, NO_BUDGET,
                       static_cast<cudaStream_t>(stream));
+}
+
+SIMLOD_API int simlod_insert_batches_host(simlod_t* h, const simlod_point* const* h_batches,
+                                          const uint64_t* counts, uint32_t n_batches,
+                                          simlod_point* d_dst, uint32_t* d_ready, void* stream,
+                                          void* copy_stream) {
+  if (!h || (n_batches && (!h_batches || !counts || !d_dst || !d_ready)) ||
+      n_batches > MAX_FUSED_BATCHES || (reinterpret_cast<uintptr_t>(d_dst) & 15u) ||
+      (reinterpret_cast<uintptr_t>(d_ready) & 3u))
+    return SIMLOD_ERR_INVALID_ARG;
+  if (h->sticky) return SIMLOD_ERR_POISONED;
+  if (n_batches == 0) return SIMLOD_OK;
+  std::vector<const simlod_point*> dst(n_batches);
+  uint64_t off = 0;
+  for (uint32_t k = 0; k < n_batches; ++k) {
+    if (counts[k] > h->cfg.max_batch_points || (counts[k] && !h_batches[k]))
+      return SIMLOD_ERR_INVALID_ARG;
+    dst[k] = d_dst + off;
+    off += counts[k];
+  }
+  if (h->base + off > (1ull << 32)) return SIMLOD_ERR_TOO_MANY_POINTS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStream_t cs = static_cast<cudaStream_t>(copy_stream);
+  // flags cleared on `stream` before the launch, and before any copy sets one
+  if (cudaMemsetAsync(d_ready, 0, sizeof(uint32_t) * n_batches, s) != cudaSuccess ||
+      cudaEventRecord(h->flags_clear, s) != cudaSuccess ||
+      cudaStreamWaitEvent(cs, h->flags_clear, 0) != cudaSuccess)
+    return poison(h, SIMLOD_ERR_CUDA);
+  // one copy per batch, then a 4-byte copy of 1 into its flag: copies of one
+  // stream run in order, so the flag is set after the batch is in place
+  for (uint32_t k = 0; k < n_batches; ++k) {
+    if (counts[k] &&
+        cudaMemcpyAsync(const_cast<simlod_point*>(dst[k]), h_batches[k],
+                        sizeof(simlod_point) * counts[k], cudaMemcpyHostToDevice,
+                        cs) != cudaSuccess)
+      return poison(h, SIMLOD_ERR_CUDA);
+    if (cudaMemcpyAsync(d_ready + k, h->one_host, sizeof(uint32_t), cudaMemcpyHostToDevice, cs) !=
+        cudaSuccess)
+      return poison(h, SIMLOD_ERR_CUDA);
+  }
+  return launch_fused(h, dst.data(), counts, n_batches, NO_BUDGET, s, d_ready);
 }
 
 SIMLOD_API int simlod_frame_update(simlod_t* h, const simlod_point* const* d_batches,
@@ -742,7 +789,8 @@ int plan_enqueue(simlod_plan_t* P, cudaStream_t s) {
   uint32_t max_iters = h->cfg.max_expand_iters ? h->cfg.max_expand_iters : h->cfg.root_log2 + 1;
   const unsigned int* n_dev = P->n_groups;
   const PlanSeg* segs = P->segs;
-  void* args[] = {&c, &bt, &n, &f, &budget, &max_iters, &n_dev, &segs};
+  const unsigned int* ready = nullptr;
+  void* args[] = {&c, &bt, &n, &f, &budget, &max_iters, &n_dev, &segs, &ready};
   if (cudaLaunchCooperativeKernel((const void*)k_fused, dim3(P->grid), dim3(FUSED_BLOCK), args,
                                   PHASE_SMEM_BYTES, s) != cudaSuccess)
     return SIMLOD_ERR_CUDA;
@@ -1336,7 +1384,9 @@ SIMLOD_API int simlod_destroy(simlod_t* h) {
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
   if (h->desc_host) cudaFreeHost(h->desc_host);
   if (h->fctl_host) cudaFreeHost(h->fctl_host);
+  if (h->one_host) cudaFreeHost(h->one_host);
   if (h->desc_done) cudaEventDestroy(h->desc_done);
+  if (h->flags_clear) cudaEventDestroy(h->flags_clear);
   delete h;
   return SIMLOD_OK;
 }

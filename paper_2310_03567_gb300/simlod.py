@@ -107,6 +107,7 @@ SIGNATURES = {
     "simlod_insert_batch": (_I32, [_P, _P, _U64, _P]),
     "simlod_insert_batch_host": (_I32, [_P, _P, _U64, _P]),
     "simlod_insert_batches": (_I32, [_P, _P, _P, _U32, _P]),
+    "simlod_insert_batches_host": (_I32, [_P, _P, _P, _U32, _P, _P, _P, _P]),
     "simlod_frame_update": (_I32, [_P, _P, _P, _U32, _U64, _P, ctypes.POINTER(_U32)]),
     "simlod_reset": (_I32, [_P, _P]),
     "simlod_sync": (_I32, [_P]),
@@ -342,6 +343,34 @@ class Octree:
         c = (ctypes.c_uint64 * max(n, 1))(*counts)
         return self._lib.simlod_insert_batches(
             self._h, p, c, n, _stream_ptr(stream if stream is not None else self.stream))
+
+    def insert_many_host(self, host_batches, dst, ready, copy_stream, stream=None,
+                         check: bool = True) -> int:
+        """Fused form fed from page-locked host memory: each batch (a pinned
+        CPU tensor of 16-byte records) is copied into `dst` (a CUDA tensor
+        with room for all of them) on copy_stream, and the persistent launch
+        starts each batch once its copy has finished (flag words in `ready`,
+        an int32 CUDA tensor with one word per batch). Asynchronous: the host
+        batches must stay alive until the launch has passed them (dst and
+        ready are kept from reuse by the caching allocator here)."""
+        n = len(host_batches)
+        s = self._order(stream)
+        for t in (dst, ready):
+            for st in (s, copy_stream):
+                if st is not None and not isinstance(st, int):
+                    t.record_stream(st)
+        total = sum(b.numel() * b.element_size() for b in host_batches)
+        if dst.numel() * dst.element_size() < total or ready.numel() < n:
+            raise ValueError("dst or ready is too small")
+        ptrs = (ctypes.c_void_p * max(n, 1))(*[b.data_ptr() for b in host_batches])
+        counts = (ctypes.c_uint64 * max(n, 1))(
+            *[b.numel() * b.element_size() // 16 for b in host_batches])
+        rc = self._lib.simlod_insert_batches_host(self._h, ptrs, counts, n, dst.data_ptr(),
+                                                  ready.data_ptr(), _stream_ptr(s),
+                                                  _stream_ptr(copy_stream))
+        if check and rc != OK:
+            raise SimlodError(rc, "simlod_insert_batches_host")
+        return rc
 
     def reset(self, stream=None):
         rc = self._lib.simlod_reset(self._h, _stream_ptr(stream if stream is not None else self.stream))

@@ -220,3 +220,79 @@ def test_morton_ordered_stream():
     assert fused_insert(t, list(w.batches())) == simlod.OK
     assert_snapshots_equal(t.snapshot(),
                            oracle.static_build(oracle.Config.make(root_log2=21), w.stream()))
+
+
+def pinned_batches(w):
+    host = torch.from_numpy(np.ascontiguousarray(w.points).view(np.uint8).reshape(-1, 16))
+    host = host.pin_memory()
+    return host, [host[int(o):int(o) + int(c)] for o, c in zip(w.offsets, w.counts)]
+
+
+@pytest.mark.parametrize("same_stream", [False, True])
+def test_host_fed_launch_waits_for_each_copy(same_stream):
+    """Host ingest pipeline: batches copied on a copy stream, the persistent
+    launch starts each batch once its ready flag is set."""
+    w = synth.aerial_workload(n=4_000_000)
+    host, parts = pinned_batches(w)
+    t = make_tree(1 << 30, root_log2=22)
+    dst = torch.empty_like(host, device="cuda")
+    ready = torch.empty(len(parts), dtype=torch.int32, device="cuda")
+    cs = t.stream if same_stream else torch.cuda.Stream()
+    t.insert_many_host(parts, dst, ready, cs)
+    assert t.sync() == simlod.OK
+    torch.cuda.synchronize()
+    assert int(ready.min().item()) == 1
+    assert torch.equal(dst.cpu(), host)
+    assert_snapshots_equal(t.snapshot(),
+                           oracle.static_build(oracle.Config.make(root_log2=22), w.points))
+    # a second stream through the same buffers continues the octree
+    t.insert_many_host(parts[:2], dst, ready, cs)
+    assert t.sync() == simlod.OK
+    both = np.concatenate([w.points, w.points[: int(w.offsets[2])]])
+    assert_snapshots_equal(t.snapshot(),
+                           oracle.static_build(oracle.Config.make(root_log2=22), both))
+
+
+def test_host_fed_launch_rejects_a_batch_outside_the_root():
+    kw = dict(root_log2=12, leaf_capacity=50, chunk_points=8, grid_log2=4)
+    pts = synth.uniform(3, 1 << 12, 4000)
+    bad = pts[1000:1500].copy()
+    bad[7] = (1, 1, -3, 0, 0, 0, 0)
+    arrays = [pts[:1000], bad, pts[1000:4000], pts[:0]]
+    host = [torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).reshape(-1, 16)).pin_memory()
+            for a in arrays]
+    t = make_tree(64 << 20, **caps(**kw))
+    dst = torch.empty((sum(len(a) for a in arrays), 16), dtype=torch.uint8, device="cuda")
+    ready = torch.empty(len(arrays), dtype=torch.int32, device="cuda")
+    t.insert_many_host(host, dst, ready, torch.cuda.Stream())
+    assert t.sync() == simlod.ERR_OUT_OF_BOUNDS
+    assert t.sync() == simlod.OK
+    assert_snapshots_equal(t.snapshot(), oracle.static_build(ocfg(**kw), pts))
+
+
+def test_host_fed_launch_times_out_on_a_flag_that_is_not_set():
+    """A ready flag that stays clear (the copy stream is held by a host
+    function for 3 s) ends the launch after the 2 s wait limit with a TIMEOUT
+    status; the GPU stays usable and a reset handle works again."""
+    import ctypes
+    import time
+
+    libcuda = ctypes.CDLL("libcuda.so.1")
+    hostfn = ctypes.CFUNCTYPE(None, ctypes.c_void_p)
+    hold = hostfn(lambda _: time.sleep(3.0))
+    w = synth.aerial_workload(n=2_000_000)
+    host, parts = pinned_batches(w)
+    t = make_tree(1 << 30, root_log2=22)
+    dst = torch.empty_like(host, device="cuda")
+    ready = torch.empty(len(parts), dtype=torch.int32, device="cuda")
+    cs = torch.cuda.Stream()
+    assert libcuda.cuLaunchHostFunc(ctypes.c_void_p(cs.cuda_stream), hold, None) == 0
+    t.insert_many_host(parts, dst, ready, cs)
+    assert t.sync() == simlod.ERR_TIMEOUT
+    assert t.insert(simlod.points_tensor(w.points[:10]), check=False) == simlod.ERR_POISONED
+    assert libcuda.cuStreamSynchronize(ctypes.c_void_p(cs.cuda_stream)) == 0
+    t.reset()
+    t.insert_many_host(parts, dst, ready, cs)
+    assert t.sync() == simlod.OK
+    assert_snapshots_equal(t.snapshot(),
+                           oracle.static_build(oracle.Config.make(root_log2=22), w.points))
