@@ -65,6 +65,12 @@ constexpr uint32_t CHUNK_HEADER = 16;
 #ifndef SL_PHASE_MIN_BLOCKS
 #define SL_PHASE_MIN_BLOCKS 2
 #endif
+#ifndef SL_STORE_PREFETCH
+#define SL_STORE_PREFETCH 1
+#endif
+#ifndef SL_COUNT_PREFETCH
+#define SL_COUNT_PREFETCH 1
+#endif
 #ifndef SL_COUNT_UNROLL
 #define SL_COUNT_UNROLL 1
 #endif
@@ -675,7 +681,16 @@ __device__ void phase_count1(const Ctx& c, uint32_t* smem, const NodeCache nc, c
   WarpBuf wb = warp_buf(smem);
   const uint32_t lane = lane_id();
   // each warp carries U units of 32 points (w, w + nwarps, ...) at a time so
-  // that their L2 round trips overlap
+  // that their L2 round trips overlap; the next units' points are loaded
+  // while the current ones descend
+#if SL_COUNT_PREFETCH
+  int4 pn[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const uint64_t i = (warp0 + j * nwarps) * 32 + lane;
+    pn[j] = i < n ? __ldcg(pts + i) : make_int4(0, 0, 0, 0);
+  }
+#endif
   for (uint64_t w0 = warp0; w0 * 32 < n; w0 += U * nwarps) {
     bool valid[U], walking[U];
     int4 p[U];
@@ -684,7 +699,13 @@ __device__ void phase_count1(const Ctx& c, uint32_t* smem, const NodeCache nc, c
     for (int j = 0; j < U; ++j) {
       const uint64_t i = (w0 + j * nwarps) * 32 + lane;
       valid[j] = i < n;
+#if SL_COUNT_PREFETCH
+      p[j] = pn[j];
+      const uint64_t inext = i + (uint64_t)U * nwarps * 32;
+      pn[j] = inext < n ? __ldcg(pts + inext) : make_int4(0, 0, 0, 0);
+#else
       p[j] = valid[j] ? __ldcg(pts + i) : make_int4(0, 0, 0, 0);
+#endif
       gidx[j] = (uint32_t)(base + i);
     }
 #pragma unroll
@@ -1323,6 +1344,17 @@ __device__ void phase_store(const Ctx& c, uint32_t* smem, const int4* pts, uint6
 #if SL_STORE_BLOCK
   if (smem) block_place_init(smem);
 #endif
+#if SL_STORE_PREFETCH
+  // the next round's cursors and points load while this round is placed
+  uint32_t node_n[U];
+  int4 p_n[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const uint64_t i = blk + j * stride + me;
+    node_n[j] = i < n ? c.b_cur[i] : 0u;
+    p_n[j] = i < n ? __ldcg(pts + i) : make_int4(0, 0, 0, 0);
+  }
+#endif
   for (uint64_t b0 = blk; b0 < n; b0 += U * stride) {
     bool valid[U];
     uint32_t node[U], ref[U], q[U];
@@ -1331,8 +1363,16 @@ __device__ void phase_store(const Ctx& c, uint32_t* smem, const int4* pts, uint6
     for (int j = 0; j < U; ++j) {
       const uint64_t i = b0 + j * stride + me;
       valid[j] = i < n;
+#if SL_STORE_PREFETCH
+      node[j] = node_n[j];
+      p[j] = p_n[j];
+      const uint64_t inext = i + (uint64_t)U * stride;
+      node_n[j] = inext < n ? c.b_cur[inext] : 0u;
+      p_n[j] = inext < n ? __ldcg(pts + inext) : make_int4(0, 0, 0, 0);
+#else
       node[j] = valid[j] ? c.b_cur[i] : 0u;
       p[j] = valid[j] ? __ldcg(pts + i) : make_int4(0, 0, 0, 0);
+#endif
       if (valid[j] && node[j] >= c.max_nodes) {
         set_error(c, E_INTERNAL);
         valid[j] = false;
