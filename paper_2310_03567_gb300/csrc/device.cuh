@@ -65,6 +65,9 @@ constexpr uint32_t CHUNK_HEADER = 16;
 #ifndef SL_PHASE_MIN_BLOCKS
 #define SL_PHASE_MIN_BLOCKS 2
 #endif
+#ifndef SL_ADVANCE_UNROLL
+#define SL_ADVANCE_UNROLL 1
+#endif
 #ifndef SL_STORE_PREFETCH
 #define SL_STORE_PREFETCH 1
 #endif
@@ -87,6 +90,7 @@ constexpr uint32_t NODE_CACHE = SL_NODE_CACHE;         // nodes mirrored in shar
 constexpr uint32_t NODE_CACHE_BYTES = NODE_CACHE * 8;  // child + grid reference
 constexpr uint32_t ZERO_UNIT = 4096;                   // bytes of grid zeroed per warp unit
 constexpr int DESCENT_GROUP = SL_DESCENT_GROUP;        // levels whose grid words load together
+constexpr int ADVANCE_U = SL_ADVANCE_UNROLL;           // advance units a warp carries at a time
 constexpr int COUNT_U = SL_COUNT_UNROLL;               // count units a warp carries at a time
 #ifndef SL_WBUF
 #define SL_WBUF 128
@@ -863,81 +867,93 @@ __device__ void phase_advance(const Ctx& c, uint32_t* smem, const NodeCache nc, 
   const uint64_t ub = first ? (n + 31) / 32 : 0;
   const uint64_t units = first ? ub + (uint64_t)t_hi * parts : ((uint64_t)n_in + 31) / 32;
   const uint4* in = first ? nullptr : c.mv[in_list];
-  for (uint64_t w = warp0; w < units; w += nwarps) {
-    bool valid = false, spill = false;
-    uint32_t idx = 0;  // batch point index or spill entry
-    uint32_t cur = 0, lvl = 0;
-    int4 p = make_int4(0, 0, 0, 0);
-    uint32_t g = 0;
-    bool have_p = false;
-    if (first && w < ub) {
-      const uint64_t i = w * 32 + lane;
-      valid = i < n;
-      idx = (uint32_t)i;
-      cur = valid ? c.b_cur[i] : 0u;
-    } else if (first) {
-      const uint64_t u = w - ub;
-      const uint32_t t = (uint32_t)(u / parts), q = (uint32_t)(u % parts) * 32u + lane;
-      const SpillTask tk = c.tasks[t];
-      const bool task_ok = ref_ok(c, tk.ref, c.chunk_bytes) && tk.n <= c.C &&
-                           (unsigned long long)tk.dst + tk.n <= c.spill_cap;
-      if (!task_ok && lane == 0) set_error(c, E_INTERNAL);
-      valid = task_ok && q < tk.n;
-      spill = true;
-      idx = tk.dst + q;
-      cur = tk.node;
-      if (valid) {
-        // the point leaves its chunk (which returns to the pool at store)
-        p = chunk_recs(c, tk.ref)[q];
-        g = chunk_aux(c, tk.ref)[q];
-        c.sp_rec[idx] = p;
-        c.sp_gidx[idx] = g;
-        have_p = true;
+  constexpr int AU = ADVANCE_U;
+  // each warp carries AU units (w, w + nwarps, ...) at a time so that their
+  // L2 round trips overlap
+  for (uint64_t w0 = warp0; w0 < units; w0 += AU * nwarps) {
+    bool valid[AU], spill[AU], have_p[AU], mv[AU];
+    uint32_t idx[AU], cur[AU], lvl[AU], g[AU], ch[AU];  // idx: batch point index or spill entry
+    int4 p[AU];
+#pragma unroll
+    for (int j = 0; j < AU; ++j) {
+      const uint64_t w = w0 + (uint64_t)j * nwarps;
+      valid[j] = spill[j] = have_p[j] = false;
+      idx[j] = cur[j] = lvl[j] = g[j] = 0;
+      p[j] = make_int4(0, 0, 0, 0);
+      if (w >= units) {
+        // past the end: nothing
+      } else if (first && w < ub) {
+        const uint64_t i = w * 32 + lane;
+        valid[j] = i < n;
+        idx[j] = (uint32_t)i;
+        cur[j] = valid[j] ? c.b_cur[i] : 0u;
+      } else if (first) {
+        const uint64_t u = w - ub;
+        const uint32_t t = (uint32_t)(u / parts), q = (uint32_t)(u % parts) * 32u + lane;
+        const SpillTask tk = c.tasks[t];
+        const bool task_ok = ref_ok(c, tk.ref, c.chunk_bytes) && tk.n <= c.C &&
+                             (unsigned long long)tk.dst + tk.n <= c.spill_cap;
+        if (!task_ok && lane == 0) set_error(c, E_INTERNAL);
+        valid[j] = task_ok && q < tk.n;
+        spill[j] = true;
+        idx[j] = tk.dst + q;
+        cur[j] = tk.node;
+        if (valid[j]) {
+          // the point leaves its chunk (which returns to the pool at store)
+          p[j] = chunk_recs(c, tk.ref)[q];
+          g[j] = chunk_aux(c, tk.ref)[q];
+          c.sp_rec[idx[j]] = p[j];
+          c.sp_gidx[idx[j]] = g[j];
+          have_p[j] = true;
+        }
+      } else {
+        const uint64_t k = w * 32 + lane;
+        if (k < n_in) {
+          const uint4 ent = in[k];
+          valid[j] = true;
+          spill[j] = (ent.x & MV_SPILL) != 0u;
+          idx[j] = ent.x & ~MV_SPILL;
+          cur[j] = ent.y;
+          lvl[j] = ent.z;
+          if (spill[j] ? idx[j] >= c.spill_cap : idx[j] >= n) {
+            set_error(c, E_INTERNAL);
+            valid[j] = false;
+          }
+        }
       }
-    } else {
-      const uint64_t k = w * 32 + lane;
-      if (k < n_in) {
-        const uint4 ent = in[k];
-        valid = true;
-        spill = (ent.x & MV_SPILL) != 0u;
-        idx = ent.x & ~MV_SPILL;
-        cur = ent.y;
-        lvl = ent.z;
-        if (spill ? idx >= c.spill_cap : idx >= n) {
-          set_error(c, E_INTERNAL);
-          valid = false;
+      if (valid[j] && cur[j] >= c.max_nodes) {
+        set_error(c, E_INTERNAL);
+        valid[j] = false;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < AU; ++j) {
+      // read a point only when its cursor node split (it moves)
+      ch[j] = valid[j] ? node_child(c, nc, cur[j]) : NONE;
+      mv[j] = ch[j] != NONE && ch[j] + 8u <= c.max_nodes;
+      if (mv[j]) {
+        if (first) lvl[j] = c.meta[cur[j]].level;
+        if (!have_p[j]) {
+          if (spill[j]) {
+            p[j] = c.sp_rec[idx[j]];
+            g[j] = c.sp_gidx[idx[j]];
+          } else {
+            p[j] = __ldcg(pts + idx[j]);
+            g[j] = (uint32_t)(base + idx[j]);
+          }
         }
       }
     }
-    if (valid && cur >= c.max_nodes) {
-      set_error(c, E_INTERNAL);
-      valid = false;
-    }
-    // read a point only when its cursor node split (it moves)
-    const uint32_t ch0 = valid ? node_child(c, nc, cur) : NONE;
-    const bool mv0 = ch0 != NONE && ch0 + 8u <= c.max_nodes;
-    if (mv0) {
-      if (first) lvl = c.meta[cur].level;
-      if (!have_p) {
-        if (spill) {
-          p = c.sp_rec[idx];
-          g = c.sp_gidx[idx];
-        } else {
-          p = __ldcg(pts + idx);
-          g = (uint32_t)(base + idx);
-        }
+    advance_items<AU>(c, wb, mv, p, g, lvl, ch, cur);
+#pragma unroll
+    for (int j = 0; j < AU; ++j) {
+      if (mv[j]) {
+        if (spill[j]) c.sp_cur[idx[j]] = cur[j];
+        else c.b_cur[idx[j]] = cur[j];
       }
+      mover_add(c, mb, out_list, mv[j],
+                make_uint4(spill[j] ? (idx[j] | MV_SPILL) : idx[j], cur[j], lvl[j] + 1u, 0u));
     }
-    const bool moving[1] = {mv0};
-    const int4 pp[1] = {p};
-    const uint32_t gidx[1] = {g}, lv[1] = {lvl}, ch[1] = {ch0};
-    uint32_t cr[1] = {cur};
-    advance_items<1>(c, wb, moving, pp, gidx, lv, ch, cr);
-    if (mv0) {
-      if (spill) c.sp_cur[idx] = cr[0];
-      else c.b_cur[idx] = cr[0];
-    }
-    mover_add(c, mb, out_list, mv0, make_uint4(spill ? (idx | MV_SPILL) : idx, cr[0], lvl + 1u, 0u));
   }
   warp_flush(c, wb);
   mover_flush(c, mb, out_list);
