@@ -1431,14 +1431,18 @@ __device__ void phase_store(const Ctx& c, uint32_t* smem, const int4* pts, uint6
     }
 #pragma unroll
     for (int j = 0; j < U; ++j) {
-      const unsigned long long key = valid[j] ? sl[j]->key : 0ull;
-      rgba[j] = valid[j] ? (uint32_t)sl[j]->val : 0u;
-      node[j] = (uint32_t)(key >> (3u * G));
-      cell[j] = (uint32_t)key & cmask;
+      const ulonglong2 kv = valid[j] ? *reinterpret_cast<const ulonglong2*>(sl[j])
+                                     : make_ulonglong2(0ull, 0ull);
+      rgba[j] = (uint32_t)kv.y;
+      node[j] = (uint32_t)(kv.x >> (3u * G));
+      cell[j] = (uint32_t)kv.x & cmask;
     }
+    int4 nm[U];  // the node's min corner and level (voxel centre), loaded with its grid ref
 #pragma unroll
     for (int j = 0; j < U; ++j) {
-      gref[j] = (valid[j] && node[j] < c.max_nodes) ? c.gridref[node[j]] : NONE;
+      const bool in = valid[j] && node[j] < c.max_nodes;
+      gref[j] = in ? c.gridref[node[j]] : NONE;
+      nm[j] = in ? *reinterpret_cast<const int4*>(&c.meta[node[j]].min[0]) : make_int4(0, 0, 0, 0);
       const bool ok = valid[j] && ref_ok(c, gref[j], c.grid_bytes);
       if (valid[j] && !ok) set_error(c, E_INTERNAL);
       valid[j] = ok;
@@ -1447,14 +1451,13 @@ __device__ void phase_store(const Ctx& c, uint32_t* smem, const int4* pts, uint6
 #pragma unroll
     for (int j = 0; j < U; ++j) {
       if (!valid[j]) continue;
-      const NodeMeta& m = c.meta[node[j]];
-      const uint32_t L = c.rlog2 - m.level;
+      const uint32_t L = c.rlog2 - (uint32_t)nm[j].w;
       const uint32_t cx = cell[j] & amask, cy = (cell[j] >> G) & amask, cz = cell[j] >> (2u * G);
       // Section 3.4: the voxel is a point at the (floor of the) cell centre
       int4 v;
-      v.x = m.min[0] + (int32_t)(((2ull * cx + 1ull) << L) >> (G + 1u));
-      v.y = m.min[1] + (int32_t)(((2ull * cy + 1ull) << L) >> (G + 1u));
-      v.z = m.min[2] + (int32_t)(((2ull * cz + 1ull) << L) >> (G + 1u));
+      v.x = nm[j].x + (int32_t)(((2ull * cx + 1ull) << L) >> (G + 1u));
+      v.y = nm[j].y + (int32_t)(((2ull * cy + 1ull) << L) >> (G + 1u));
+      v.z = nm[j].z + (int32_t)(((2ull * cz + 1ull) << L) >> (G + 1u));
       v.w = (int32_t)rgba[j];
       put_rec(c, ref[j], q[j], v, cell[j]);
       atomicOr(grid_words(c, gref[j]) + (cell[j] >> 5), 1u << (cell[j] & 31u));
