@@ -65,6 +65,9 @@ constexpr uint32_t CHUNK_HEADER = 16;
 #ifndef SL_PHASE_MIN_BLOCKS
 #define SL_PHASE_MIN_BLOCKS 2
 #endif
+#ifndef SL_HASH_BUCKET
+#define SL_HASH_BUCKET 0
+#endif
 #ifndef SL_ADVANCE_UNROLL
 #define SL_ADVANCE_UNROLL 1
 #endif
@@ -424,6 +427,19 @@ __device__ __forceinline__ ulonglong2 slot_load(const HSlot* s) {
   return kv;
 }
 
+// First claim-table slot of a key (node << 3G | cell). With SL_HASH_BUCKET,
+// runs of 2^SL_HASH_BUCKET cells along x share one randomly placed bucket of
+// slots, so the neighbouring cells that a warp claims fall on a few cache
+// lines; otherwise every key is placed at random.
+__device__ __forceinline__ uint32_t claim_slot(const Ctx& c, unsigned long long key) {
+#if SL_HASH_BUCKET
+  constexpr uint32_t B = SL_HASH_BUCKET;
+  return (((uint32_t)fmix64(key >> B) << B) | ((uint32_t)key & ((1u << B) - 1u))) & c.hash_mask;
+#else
+  return (uint32_t)fmix64(key) & c.hash_mask;
+#endif
+}
+
 // Probes after the first for `key` (slot h held another key): returns true,
 // with the slot in h, when this call put the key into the table (the cell is
 // new in this update); a slot already holding the key is lowered to val if
@@ -593,7 +609,7 @@ __device__ __forceinline__ void warp_claim_global(const Ctx& c, WarpBuf& wb, con
   unsigned long long k0[N], v0[N];
 #pragma unroll
   for (int j = 0; j < N; ++j) {
-    h[j] = (uint32_t)fmix64(key[j]) & c.hash_mask;
+    h[j] = claim_slot(c, key[j]);
     k0[j] = v0[j] = 0ull;
     if (lead[j]) {
       const ulonglong2 kv = slot_load(c.hash + h[j]);
