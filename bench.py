@@ -624,24 +624,43 @@ def run_serving(args):
     cap = cal.report()["mpts_per_s"] * 1e6
     cal.close()
     rate = 0.7 * cap
-    reqs = serving.poisson_requests(streams, 100_000, 5_000_000, rate, seed=7)
+    # several independent Poisson traces (each the whole stream of every
+    # octree); latency percentiles pool their requests, since a p99 over one
+    # trace rests on its two or three slowest requests
+    traces = [serving.poisson_requests(streams, 100_000, 5_000_000, rate, seed=7 + t)
+              for t in range(args.serving_traces)]
+    reqs = traces[0]
     arenas = sum(simlod.arena_bytes(sp.cfg, sp.data_bytes) for sp in specs)
     budget = arenas + (4 << 30)
     out = {}
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     for name, plain in (("serving", False), ("plain", True)):
-        for r in reqs:
-            r.admitted = r.done = -1.0
-        srv = serving.Server(specs, hbm_budget=budget, compute_slots=2, frame_ms=33.3,
-                             plain=plain)
-        if not plain:
-            clocks.start()
-        srv.run(reqs)
-        if not plain:
-            clk = clocks.stop()
-        out[name] = srv.report()
-        srv.close()
-        torch.cuda.empty_cache()
+        lat, wait, reps = [], [], []
+        for t, tr in enumerate(traces):
+            for r in tr:
+                r.admitted = r.done = -1.0
+            srv = serving.Server(specs, hbm_budget=budget, compute_slots=2, frame_ms=33.3,
+                                 plain=plain)
+            if not plain and t == 0:
+                clocks.start()
+            done = srv.run(tr)
+            if not plain and t == 0:
+                clk = clocks.stop()
+            lat += [(r.done - r.arrival) * 1e3 for r in done]
+            wait += [(r.admitted - r.arrival) * 1e3 for r in done]
+            reps.append(srv.report())
+            srv.close()
+            torch.cuda.empty_cache()
+        rep = dict(reps[0])
+        rep["traces"] = len(traces)
+        rep["requests"] = len(lat)
+        rep["mpts_per_s"] = float(np.mean([x["mpts_per_s"] for x in reps]))
+        rep["latency_ms"] = {"p50": float(np.percentile(lat, 50)),
+                             "p99": float(np.percentile(lat, 99)),
+                             "p99_per_trace": [x["latency_ms"]["p99"] for x in reps]}
+        rep["admission_wait_ms"] = {"p50": float(np.percentile(wait, 50)),
+                                    "p99": float(np.percentile(wait, 99))}
+        out[name] = rep
     # saturated: the whole trace queued at once (throughput at capacity)
     sat = {}
     for name, plain in (("serving", False), ("plain", True)):
@@ -663,7 +682,8 @@ def run_serving(args):
         "warmup": 0, "ms_per_step": sv["seconds"] * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": f"serving-16 octrees ({total} points, scale {args.serving_scale})",
-                   "requests": len(reqs), "request_points": "log-uniform 100k-5M",
+                   "requests": len(reqs), "traces": len(traces),
+                   "request_points": "log-uniform 100k-5M",
                    "arrival": f"Poisson, {rate / 1e6:.0f} Mpts/s (70% of plain capacity "
                               f"{cap / 1e6:.0f} Mpts/s)",
                    "hbm_budget_bytes": budget, "frame": "1920x1080 render of every octree "
@@ -759,6 +779,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="aerial",
                     choices=["aerial", "uniform", "clustered", "mixed", "serving"])
+    ap.add_argument("--serving-traces", type=int, default=3,
+                    help="independent Poisson traces whose requests the serving latency pools")
     ap.add_argument("--serving-scale", type=float, default=0.25,
                     help="octree sizes of the serving workload relative to 5M-200M points")
     ap.add_argument("--points", type=int, default=None)

@@ -5,8 +5,10 @@ the updates (Section 7.2's interleaving of updates and frames).
 
 Every octree has its own CUDA stream and arena. A request (points of one
 octree, in pinned host memory) is admitted when its device copy fits the HBM
-budget left by the arenas and the requests in flight; it is copied on its
-octree's stream. When a launch slot is free, the octree with the oldest
+budget left by the arenas and the requests in flight; it is copied on the
+server's copy stream, so that the copy overlaps the launches running on its
+octree's stream, and the launch that applies it waits for the copy's event.
+When a launch slot is free, the octree with the oldest
 admitted request gets one fused launch (simlod_insert_batches) over all of its
 admitted requests, each request one batch, in arrival order. At most
 `compute_slots` launches are in flight, and each handle's persistent launch
@@ -40,6 +42,7 @@ class Request:
     admitted: float = -1.0
     done: float = -1.0
     dev: object = None  # device copy while in flight
+    ready: object = None  # event: the device copy is complete
 
     @property
     def n(self) -> int:
@@ -90,6 +93,7 @@ class Server:
             self.frames.append(None)
         if self.used > self.budget:
             raise ValueError("the arenas alone exceed the HBM budget")
+        self.copy_stream = torch.cuda.Stream()
         self.pending = []      # arrived, not admitted (arrival order)
         self.queued = [[] for _ in self.trees]   # admitted, not launched, per octree
         self.inflight = []     # (event, octree, requests)
@@ -111,7 +115,7 @@ class Server:
                 t = self.now()
                 for r in reqs:
                     r.done = t
-                    r.dev = None
+                    r.dev = r.ready = None
                     self.used -= r.nbytes
                     self.finished.append(r)
                 self.busy[k] = False
@@ -123,10 +127,11 @@ class Server:
         torch = self.torch
         while self.pending and self.used + self.pending[0].nbytes <= self.budget:
             r = self.pending.pop(0)
-            tree = self.trees[r.octree]
-            with torch.cuda.stream(tree.stream):
+            with torch.cuda.stream(self.copy_stream):
                 r.dev = torch.empty_like(r.points, device="cuda")
                 r.dev.copy_(r.points, non_blocking=True)
+                r.ready = torch.cuda.Event()
+                r.ready.record(self.copy_stream)
             self.used += r.nbytes
             r.admitted = self.now()
             self.queued[r.octree].append(r)
@@ -141,6 +146,9 @@ class Server:
             reqs = self.queued[k][: self.max_batches]
             self.queued[k] = self.queued[k][self.max_batches:]
             tree = self.trees[k]
+            for r in reqs:
+                tree.stream.wait_event(r.ready)
+                r.dev.record_stream(tree.stream)
             if self.plain:
                 rc = tree.insert(reqs[0].dev, stream=tree.stream, check=False)
             else:
