@@ -210,6 +210,14 @@ def check_invariants(snap, stream_pts: np.ndarray, root_min, root_log2, T, C, G)
     return True
 
 
+def check_allocator(snap, stats):
+    """Chunk allocator accounting at rest (I4, second half): every chunk taken
+    from the data region is either in exactly one node's list or in the pool."""
+    live = int(snap.nodes["n_chunks"].astype(np.int64).sum())
+    assert live + int(stats["chunks_pool"]) == int(stats["chunks_bumped"]), \
+        (live, stats["chunks_pool"], stats["chunks_bumped"])
+
+
 def assert_snapshots_equal(a, b):
     assert np.array_equal(a.nodes, b.nodes), _first_diff(a.nodes, b.nodes)
     assert np.array_equal(a.points, b.points), _first_diff(a.points, b.points)

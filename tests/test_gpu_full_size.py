@@ -12,7 +12,7 @@ import pytest
 
 import bench
 import oracle
-from helpers import assert_snapshots_equal
+from helpers import assert_snapshots_equal, check_allocator
 from paper_2310_03567_gb300 import simlod
 
 pytestmark = pytest.mark.gpu
@@ -31,6 +31,7 @@ def test_full_size_fused_launch_matches_oracle(name):
     st = tree.stats()
     assert st["points"] == w.n_points and st["batches"] == len(w.counts)
     snap = tree.snapshot()
+    check_allocator(snap, st)
     tree.close()
     del dev
     ref = oracle.static_build(oracle.Config.make(root_min=w.root_min, root_log2=root_log2),

@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import assert_snapshots_equal, check_invariants, load_golden, points_array
+from helpers import (assert_snapshots_equal, check_allocator, check_invariants, load_golden,
+                     points_array)
 from paper_2310_03567_gb300 import simlod, synth
 
 pytestmark = pytest.mark.gpu
@@ -125,13 +126,15 @@ def test_aerial_and_clustered_one_launch():
     w = synth.aerial_workload(n=6_000_000)
     t = make_tree(4 << 30, root_log2=22)
     assert fused_insert(t, list(w.batches())) == simlod.OK
-    assert_snapshots_equal(t.snapshot(),
-                           oracle.static_build(oracle.Config.make(root_log2=22), w.points))
+    snap = t.snapshot()
+    check_allocator(snap, t.stats())
+    assert_snapshots_equal(snap, oracle.static_build(oracle.Config.make(root_log2=22), w.points))
     w = synth.clustered_workload(n=8_000_000, n_quads=600, batch_lo=200_000, batch_hi=2_000_000)
     t = make_tree(4 << 30, root_log2=21)
     assert fused_insert(t, list(w.batches())) == simlod.OK
-    assert_snapshots_equal(t.snapshot(),
-                           oracle.static_build(oracle.Config.make(root_log2=21), w.stream()))
+    snap = t.snapshot()
+    check_allocator(snap, t.stats())
+    assert_snapshots_equal(snap, oracle.static_build(oracle.Config.make(root_log2=21), w.stream()))
 
 
 def test_rejected_batch_inside_a_launch_is_skipped():
@@ -242,6 +245,7 @@ def test_host_fed_launch_waits_for_each_copy(same_stream):
     assert t.sync() == simlod.OK
     torch.cuda.synchronize()
     assert int(ready.min().item()) == 1
+    check_allocator(t.snapshot(), t.stats())
     assert torch.equal(dst.cpu(), host)
     assert_snapshots_equal(t.snapshot(),
                            oracle.static_build(oracle.Config.make(root_log2=22), w.points))

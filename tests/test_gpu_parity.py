@@ -11,8 +11,8 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import (assert_snapshots_equal, check_invariants, compare_to_brute, load_golden,
-                     pack_rgba, points_array)
+from helpers import (assert_snapshots_equal, check_allocator, check_invariants, compare_to_brute,
+                     load_golden, pack_rgba, points_array)
 from paper_2310_03567_gb300 import simlod, synth
 
 pytestmark = pytest.mark.gpu
@@ -145,6 +145,7 @@ def test_random_configs_every_batch(case):
     check_invariants(snap, pts, (0, 0, 0), L, T, C, G)
     st = tree.stats()
     assert st["points"] == n and st["batches"] == len(cuts) - 1
+    check_allocator(snap, st)
 
 
 # -------------------------------------------------------- paper-size cases
@@ -170,6 +171,7 @@ def test_aerial_prefix_bit_exact():
     for b in w.batches():
         tree.insert(simlod.points_tensor(b))
     snap = tree.snapshot()
+    check_allocator(snap, tree.stats())
     same(snap, oracle.static_build(oracle.Config.make(root_log2=22), w.points))
 
 
