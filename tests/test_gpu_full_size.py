@@ -38,3 +38,30 @@ def test_full_size_fused_launch_matches_oracle(name):
                               w.stream())
     assert_snapshots_equal(snap, ref)
     assert int(snap.nodes["n_voxels"].sum()) == st["voxels"]
+
+
+def test_full_size_batched_form_matches_oracle():
+    """The batched form on the 100M-point mixed stream (terrain and clustered
+    runs, uneven batches of 64k-8M points) with the parameters the autotuner
+    picks there (merged updates up to the largest batch, 2 blocks per SM,
+    CUDA graph): the octree equals the oracle's closed form of the stream."""
+    w, root_log2 = bench.make_workload("mixed", None)
+    dev = simlod.points_tensor(w.points)
+    tree = bench.make_octree(w, root_log2)
+    ptrs = [dev.data_ptr() + int(o) * 16 for o in w.offsets]
+    counts = [int(c) for c in w.counts]
+    plan = tree.plan(ptrs, counts, merge_points=max(counts), blocks_per_sm=2, use_graph=True)
+    for _ in range(2):  # a replay after a reset gives the same octree
+        tree.reset()
+        assert plan.run() == simlod.OK
+    assert tree.sync() == simlod.OK
+    st = tree.stats()
+    assert st["points"] == w.n_points
+    snap = tree.snapshot()
+    check_allocator(snap, st)
+    plan.close()
+    tree.close()
+    del dev
+    ref = oracle.static_build(oracle.Config.make(root_min=w.root_min, root_log2=root_log2),
+                              w.stream())
+    assert_snapshots_equal(snap, ref)
