@@ -300,3 +300,25 @@ def test_host_fed_launch_times_out_on_a_flag_that_is_not_set():
     assert t.sync() == simlod.OK
     assert_snapshots_equal(t.snapshot(),
                            oracle.static_build(oracle.Config.make(root_log2=22), w.points))
+
+
+def test_most_batches_per_launch_and_one_more():
+    """16,384 batches in one launch (the limit; most of them a single point,
+    some empty) give the oracle's octree; 16,385 are refused with
+    INVALID_ARG before anything is enqueued."""
+    kw = dict(root_log2=16, leaf_capacity=300, chunk_points=40, grid_log2=5)
+    n_b = 16_384
+    rng = np.random.default_rng(5)
+    sizes = rng.choice([0, 1, 1, 1, 2, 7], n_b)
+    pts = synth.uniform(17, 1 << 16, int(sizes.sum()))
+    t = make_tree(256 << 20, **caps(**kw))
+    dev = simlod.points_tensor(pts)
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+    ptrs = [dev.data_ptr() + int(o) * 16 for o in offs]
+    assert t.insert_many_ptrs(ptrs + ptrs[:1], [int(c) for c in sizes] + [1]) == \
+        simlod.ERR_INVALID_ARG
+    assert t.insert_many_ptrs(ptrs, [int(c) for c in sizes]) == simlod.OK
+    assert t.sync() == simlod.OK
+    st = t.stats()
+    assert st["points"] == len(pts) and st["batches"] == int((sizes > 0).sum())
+    assert_snapshots_equal(t.snapshot(), oracle.static_build(ocfg(**kw), pts))
