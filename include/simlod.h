@@ -67,7 +67,7 @@ typedef struct {
   uint64_t max_batch_points; /* largest n accepted by one insert, 1..2^31-1 */
   uint64_t spill_capacity;   /* points re-inserted from split leaves, per update, < 2^31 */
   uint64_t backlog_capacity; /* new voxels per update (10M suggested; Section 5.2) */
-  uint64_t max_nodes;        /* node table size */
+  uint64_t max_nodes;        /* node table size (9 .. 2^27) */
   uint32_t flags;            /* reserved, 0 */
   uint32_t reserved;
 } simlod_config;

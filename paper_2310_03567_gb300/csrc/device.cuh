@@ -103,7 +103,7 @@ constexpr int PHASE_BLOCK = SL_PHASE_BLOCK;            // threads of count / adv
 constexpr int PHASE_MIN_BLOCKS = SL_PHASE_MIN_BLOCKS;  // resident blocks per SM they aim for
 // dynamic shared memory of the count / advance / fused blocks
 #ifndef SL_MVBUF
-#define SL_MVBUF 128
+#define SL_MVBUF 256
 #endif
 constexpr uint32_t MVBUF = SL_MVBUF;                    // mover-list entries staged per warp
 constexpr uint32_t TALLY_LOG2 = 9;                      // block tally cache: 512 nodes
@@ -112,7 +112,7 @@ constexpr uint32_t TALLY_SLOTS = 1u << TALLY_LOG2;
 // new-cell staging, mover staging, block tally cache
 constexpr uint32_t SMEM_WBUF = 2 * NODE_CACHE;                        // in u32 words
 constexpr uint32_t SMEM_MVBUF = SMEM_WBUF + (PHASE_BLOCK / 32) * WBUF;
-constexpr uint32_t SMEM_TALLY = SMEM_MVBUF + (PHASE_BLOCK / 32) * MVBUF * 4;
+constexpr uint32_t SMEM_TALLY = SMEM_MVBUF + (PHASE_BLOCK / 32) * MVBUF * 2;
 constexpr uint32_t PHASE_SMEM_BYTES = 4 * (SMEM_TALLY + 2 * TALLY_SLOTS);
 
 // Sticky device error bits.
@@ -210,7 +210,7 @@ struct Ctx {
   uint32_t* sp_gidx;  //   and its gidx
   uint32_t* b_cur;    // per batch point: cursor node
   uint32_t* scur;     // per node: store cursor of the current update
-  uint4* mv[2];       // mover lists: points that moved in the last advance round
+  uint2* mv[2];       // mover lists: points that moved in the last advance round
   HSlot* hash;
   uint32_t* keys;     // backlog: table slots of this update's new cells
   uint8_t* data;
@@ -554,13 +554,13 @@ __device__ __forceinline__ void warp_flush(const Ctx& c, WarpBuf& wb) {
 // and the new-cell staging), appended to the list with one atomicAdd per
 // flush: one reservation per MVBUF movers instead of one per warp unit.
 struct MoverBuf {
-  uint4* buf;
+  uint2* buf;
   uint32_t n;  // staged entries (the same value in every lane)
 };
 
 __device__ __forceinline__ MoverBuf mover_buf(uint32_t* smem) {
   MoverBuf mb;
-  mb.buf = reinterpret_cast<uint4*>(smem + SMEM_MVBUF) + (threadIdx.x / 32) * MVBUF;
+  mb.buf = reinterpret_cast<uint2*>(smem + SMEM_MVBUF) + (threadIdx.x / 32) * MVBUF;
   mb.n = 0;
   return mb;
 }
@@ -583,7 +583,7 @@ __device__ __forceinline__ void mover_flush(const Ctx& c, MoverBuf& mb, int list
 
 // All 32 lanes call: lanes with `moved` stage entry `ent`.
 __device__ __forceinline__ void mover_add(const Ctx& c, MoverBuf& mb, int list, bool moved,
-                                          uint4 ent) {
+                                          uint2 ent) {
   const unsigned mm = __ballot_sync(FULL_MASK, moved);
   if (mm == 0u) return;
   const uint32_t k = (uint32_t)__popc(mm);
@@ -836,10 +836,12 @@ __device__ __forceinline__ void advance_items(const Ctx& c, WarpBuf& wb, const b
   }
 }
 
-// A mover-list entry (16 bytes) is a point whose cursor moved in the last
+// A mover-list entry (8 bytes) is a point whose cursor moved in the last
 // advance round: x = MV_SPILL | spill entry, or a batch point index; y = its
-// cursor node; z = that node's level.
+// cursor node (MV_NODE_BITS bits) | that node's level << MV_NODE_BITS.
 constexpr uint32_t MV_SPILL = 1u << 31;
+constexpr uint32_t MV_NODE_BITS = 27;  // node ids below 2^27 (the node table limit)
+constexpr uint32_t MV_NODE_MASK = (1u << MV_NODE_BITS) - 1u;
 
 // Advance round r of the expansion (r >= 2 counts decide rounds): zero the
 // grids of the splits [s_lo, s_hi) of the previous decide, then move every
@@ -882,7 +884,7 @@ __device__ void phase_advance(const Ctx& c, uint32_t* smem, const NodeCache nc, 
   const bool first = in_list < 0;
   const uint64_t ub = first ? (n + 31) / 32 : 0;
   const uint64_t units = first ? ub + (uint64_t)t_hi * parts : ((uint64_t)n_in + 31) / 32;
-  const uint4* in = first ? nullptr : c.mv[in_list];
+  const uint2* in = first ? nullptr : c.mv[in_list];
   constexpr int AU = ADVANCE_U;
   // each warp carries AU units (w, w + nwarps, ...) at a time so that their
   // L2 round trips overlap
@@ -925,12 +927,12 @@ __device__ void phase_advance(const Ctx& c, uint32_t* smem, const NodeCache nc, 
       } else {
         const uint64_t k = w * 32 + lane;
         if (k < n_in) {
-          const uint4 ent = in[k];
+          const uint2 ent = in[k];
           valid[j] = true;
           spill[j] = (ent.x & MV_SPILL) != 0u;
           idx[j] = ent.x & ~MV_SPILL;
-          cur[j] = ent.y;
-          lvl[j] = ent.z;
+          cur[j] = ent.y & MV_NODE_MASK;
+          lvl[j] = ent.y >> MV_NODE_BITS;
           if (spill[j] ? idx[j] >= c.spill_cap : idx[j] >= n) {
             set_error(c, E_INTERNAL);
             valid[j] = false;
@@ -968,7 +970,8 @@ __device__ void phase_advance(const Ctx& c, uint32_t* smem, const NodeCache nc, 
         else c.b_cur[idx[j]] = cur[j];
       }
       mover_add(c, mb, out_list, mv[j],
-                make_uint4(spill[j] ? (idx[j] | MV_SPILL) : idx[j], cur[j], lvl[j] + 1u, 0u));
+                make_uint2(spill[j] ? (idx[j] | MV_SPILL) : idx[j],
+                           cur[j] | ((lvl[j] + 1u) << MV_NODE_BITS)));
     }
   }
   warp_flush(c, wb);

@@ -174,7 +174,7 @@ bool valid_config(const simlod_config* c) {
   if (c->spill_capacity >= (1ull << 31) || c->backlog_capacity < 1 ||
       c->backlog_capacity > (1ull << 31))
     return false;
-  if (c->max_nodes < 9 || c->max_nodes > (1ull << 31)) return false;
+  if (c->max_nodes < 9 || c->max_nodes > (1ull << MV_NODE_BITS)) return false;
   if ((c->leaf_capacity + (uint64_t)c->chunk_points - 1) / c->chunk_points > (1u << 18))
     return false;  // chunk directories of at most 1 MiB
   for (int a = 0; a < 3; ++a) {
@@ -226,8 +226,8 @@ bool plan_layout(const simlod_config* c, size_t arena_bytes, Layout* L) {
   L->splits = take(sizeof(SplitEntry) * L->max_splits);
   L->sp_cur = take(4 * S);
   L->b_cur = take(4 * B);
-  L->mv0 = take(16 * (B + S));
-  L->mv1 = take(16 * (B + S));
+  L->mv0 = take(8 * (B + S));
+  L->mv1 = take(8 * (B + S));
   L->sp_rec = take(16 * S);
   L->sp_gidx = take(4 * S);
   L->scur = take(4 * N);
@@ -274,8 +274,8 @@ void make_ctx(simlod_t* h) {
   c.tasks = reinterpret_cast<SpillTask*>(a + L.tasks);
   c.sp_cur = reinterpret_cast<uint32_t*>(a + L.sp_cur);
   c.b_cur = reinterpret_cast<uint32_t*>(a + L.b_cur);
-  c.mv[0] = reinterpret_cast<uint4*>(a + L.mv0);
-  c.mv[1] = reinterpret_cast<uint4*>(a + L.mv1);
+  c.mv[0] = reinterpret_cast<uint2*>(a + L.mv0);
+  c.mv[1] = reinterpret_cast<uint2*>(a + L.mv1);
   c.sp_rec = reinterpret_cast<int4*>(a + L.sp_rec);
   c.sp_gidx = reinterpret_cast<uint32_t*>(a + L.sp_gidx);
   c.scur = reinterpret_cast<uint32_t*>(a + L.scur);
