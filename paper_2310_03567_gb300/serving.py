@@ -9,13 +9,19 @@ budget left by the arenas and the requests in flight; it is copied on the
 server's copy stream, so that the copy overlaps the launches running on its
 octree's stream, and the launch that applies it waits for the copy's event.
 When a launch slot is free, the octree with the oldest
-admitted request gets one fused launch (simlod_insert_batches) over all of its
-admitted requests, each request one batch, in arrival order. At most
+admitted request gets one fused launch (simlod_insert_batches) over its
+admitted requests, each request one batch, in arrival order, up to
+max_points_per_launch points (which bounds how long the requests of other
+octrees wait for a slot). At most
 `compute_slots` launches are in flight, and each handle's persistent launch
 uses 1 / compute_slots of every SM, so that the launches in flight always fit
 on the GPU together (their grid barriers wait for all of their blocks). Frames
 are enqueued on each octree's stream after the updates before them, so a
-frame shows every request completed before it and none half-applied.
+frame shows every request completed before it and none half-applied. A frame
+that is due holds new launches back until the launches in flight have
+finished and renders alone: render blocks that took SM slots beside one
+persistent launch would hold back the next persistent launch, which needs a
+slot on every SM.
 
 Requests of one octree are applied in arrival order, which fixes their gidx:
 each octree ends up exactly as if its requests had been inserted alone, one
@@ -62,7 +68,8 @@ class OctreeSpec:
 
 class Server:
     def __init__(self, specs, hbm_budget: int, compute_slots: int = 2, frame_ms: float = 0.0,
-                 max_batches_per_launch: int = 64, plain: bool = False):
+                 max_batches_per_launch: int = 64, max_points_per_launch: int = 8_000_000,
+                 plain: bool = False):
         """plain=True serves with the plain per-kernel path instead: one
         request per update, one update at a time (the baseline)."""
         import torch
@@ -77,6 +84,8 @@ class Server:
         self.slots = compute_slots
         self.frame_ms = frame_ms
         self.max_batches = max_batches_per_launch
+        # bounds a launch's duration, and so the wait of requests behind it
+        self.max_points = max_points_per_launch
         self.trees, self.cams, self.frames = [], [], []
         for sp in specs:
             arena = simlod.make_arena(sp.cfg, sp.data_bytes)
@@ -100,6 +109,7 @@ class Server:
         self.busy = [False] * len(self.trees)
         self.finished = []
         self.frame_times = []
+        self.frame_waits = []
         self.launches = 0
         self.t0 = None
 
@@ -143,8 +153,11 @@ class Server:
             if not ready:
                 return
             k = min(ready, key=lambda j: self.queued[j][0].arrival)
-            reqs = self.queued[k][: self.max_batches]
-            self.queued[k] = self.queued[k][self.max_batches:]
+            q, take, pts = self.queued[k], 0, 0
+            while take < min(len(q), self.max_batches) and (take == 0 or pts + q[take].n <= self.max_points):
+                pts += q[take].n
+                take += 1
+            reqs, self.queued[k] = q[:take], q[take:]
             tree = self.trees[k]
             for r in reqs:
                 tree.stream.wait_event(r.ready)
@@ -192,7 +205,7 @@ class Server:
         self.t0 = time.perf_counter()
         nxt = 0
         next_frame = self.frame_ms / 1e3 if self.frame_ms else None
-        frame_evs, frame_t = [], 0.0
+        frame_evs, frame_t, due_t = [], 0.0, None
         while nxt < len(reqs) or self.pending or any(self.queued) or self.inflight:
             t = self.now()
             while nxt < len(reqs) and reqs[nxt].arrival <= t:
@@ -200,10 +213,18 @@ class Server:
                 nxt += 1
             self._poll()
             self._admit()
-            self._launch()
-            if next_frame is not None and t >= next_frame and not frame_evs:
-                frame_evs, frame_t = self.render_frame(), t
+            # a frame that is due holds new launches back until the launches in
+            # flight are done, then renders alone: a render's blocks never
+            # occupy the SM slots a persistent launch needs on every SM
+            if next_frame is not None and t >= next_frame and due_t is None and not frame_evs:
+                due_t = t
                 next_frame += self.frame_ms / 1e3
+            if due_t is not None and not self.inflight:
+                frame_evs, frame_t = self.render_frame(), self.now()
+                self.frame_waits.append(frame_t - due_t)
+                due_t = None
+            if due_t is None and not frame_evs:
+                self._launch()
             if frame_evs and all(e.query() for e in frame_evs):
                 self.frame_times.append(self.now() - frame_t)
                 frame_evs = []
@@ -222,6 +243,7 @@ class Server:
         pts = sum(r.n for r in self.finished)
         span = max(r.done for r in self.finished) - min(r.arrival for r in self.finished)
         ft = np.array(self.frame_times) * 1e3 if self.frame_times else np.zeros(1)
+        fw = np.array(self.frame_waits) * 1e3 if self.frame_waits else np.zeros(1)
         return {"requests": len(self.finished), "points": pts, "seconds": span,
                 "mpts_per_s": pts / span / 1e6 if span > 0 else 0.0,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)),
@@ -230,7 +252,9 @@ class Server:
                                       "p99": float(np.percentile(wait, 99))},
                 "launches": self.launches, "frames": len(self.frame_times),
                 "frame_ms": {"p50": float(np.percentile(ft, 50)),
-                             "p99": float(np.percentile(ft, 99))}}
+                             "p99": float(np.percentile(ft, 99))},
+                "frame_wait_ms": {"p50": float(np.percentile(fw, 50)),
+                                  "p99": float(np.percentile(fw, 99))}}
 
     def close(self):
         for t in self.trees:
