@@ -153,10 +153,8 @@ class Server:
             if not ready:
                 return
             k = min(ready, key=lambda j: self.queued[j][0].arrival)
-            q, take, pts = self.queued[k], 0, 0
-            while take < min(len(q), self.max_batches) and (take == 0 or pts + q[take].n <= self.max_points):
-                pts += q[take].n
-                take += 1
+            q = self.queued[k]
+            take = launch_take([r.n for r in q], self.max_batches, self.max_points)
             reqs, self.queued[k] = q[:take], q[take:]
             tree = self.trees[k]
             for r in reqs:
@@ -259,6 +257,17 @@ class Server:
     def close(self):
         for t in self.trees:
             t.close()
+
+
+def launch_take(sizes, max_batches: int, max_points: int) -> int:
+    """How many queued requests (sizes in points, oldest first) one launch
+    takes: at least one, at most max_batches, and no more than max_points
+    points unless the first request alone is larger."""
+    take, pts = 0, 0
+    while take < min(len(sizes), max_batches) and (take == 0 or pts + sizes[take] <= max_points):
+        pts += sizes[take]
+        take += 1
+    return take
 
 
 def poisson_requests(streams, sizes_lo: int, sizes_hi: int, rate_pts_per_s: float, seed: int):
