@@ -133,11 +133,6 @@ def compare_to_brute(snap, stream, root_min, root_log2, T, C, G):
             assert g["points"] == w["points"], (g["min"], g["points"], w["points"])
 
 
-def stream_tuples(pts: np.ndarray):
-    rgba = rgba_of(pts)
-    return [(int(p["x"]), int(p["y"]), int(p["z"]), int(c)) for p, c in zip(pts, rgba)]
-
-
 # ----------------------------------------------------------------- invariants
 
 def check_invariants(snap, stream_pts: np.ndarray, root_min, root_log2, T, C, G):

@@ -16,9 +16,8 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import (brute_force, check_invariants, compare_to_brute, load_golden,
-                     pack_rgba, points_array, snapshot_to_dicts, stream_tuples,
-                     assert_snapshots_equal)
+from helpers import (assert_snapshots_equal, brute_force, check_invariants, compare_to_brute,
+                     load_golden, pack_rgba, points_array, snapshot_to_dicts)
 from paper_2310_03567_gb300 import synth
 
 
