@@ -71,11 +71,16 @@ def test_arena_bytes_and_invalid_configs(lib):
     a = simlod.arena_bytes(cfg, 1 << 30)
     assert a > (1 << 30)
     for bad in (dict(root_log2=0), dict(root_log2=32), dict(grid_log2=8), dict(chunk_points=0),
-                dict(leaf_capacity=0), dict(max_nodes=4), dict(backlog_capacity=0)):
+                dict(leaf_capacity=0), dict(max_nodes=4), dict(max_nodes=(1 << 27) + 1),
+                dict(backlog_capacity=0)):
         c = simlod.default_config(**bad)
         out = ctypes.c_uint64()
         assert lib.simlod_arena_bytes(ctypes.byref(c), 1 << 20, ctypes.byref(out)) == \
             simlod.ERR_INVALID_ARG, bad
+    # the largest node table (mover entries pack a node id into 27 bits)
+    c = simlod.default_config(max_nodes=1 << 27)
+    out = ctypes.c_uint64()
+    assert lib.simlod_arena_bytes(ctypes.byref(c), 1 << 30, ctypes.byref(out)) == simlod.OK
     # a root cube running past int32 is invalid
     c = simlod.default_config(root_min=(2**31 - 10, 0, 0), root_log2=10)
     out = ctypes.c_uint64()
