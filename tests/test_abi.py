@@ -102,6 +102,33 @@ def test_create_rejects_bad_arguments_before_cuda(lib):
     assert lib.simlod_destroy(None) == simlod.ERR_INVALID_ARG
 
 
+def test_null_handles_are_rejected_before_cuda(lib):
+    """Every entry point that takes a handle or a plan refuses a null one with
+    INVALID_ARG, touching nothing (this machine has no GPU)."""
+    calls = {
+        "simlod_insert_batch_host": (None, None, 0, None),
+        "simlod_insert_batches": (None, None, None, 0, None),
+        "simlod_insert_batches_host": (None, None, None, 0, None, None, None, None),
+        "simlod_plan_create": (None, None, None, 0, None, None),
+        "simlod_plan_run": (None, None),
+        "simlod_plan_info": (None, None, None),
+        "simlod_plan_destroy": (None,),
+        "simlod_plan_autotune": (None, None, None, 0, None, None, None),
+        "simlod_set_launch_width": (None, 1, None),
+        "simlod_frame_update": (None, None, None, 0, 0, None, None),
+        "simlod_reset": (None, None),
+        "simlod_sync": (None,),
+        "simlod_get_stats": (None, None),
+        "simlod_snapshot": (None, None),
+        "simlod_render": (None, None, 1, 1, None, 0, None),
+        "simlod_restore": (None, None, None),
+        "simlod_set_timing": (None, 1, 0),
+        "simlod_get_timing": (None, None),
+    }
+    for name, args in calls.items():
+        assert getattr(lib, name)(*args) == simlod.ERR_INVALID_ARG, name
+
+
 def test_status_strings(lib):
     for code in range(-11, 1):
         s = simlod.status_string(code)
