@@ -4,7 +4,15 @@
 One step = one pass of the whole update path over the workload: reset the
 octree, then insert every batch of the stream (count, split, voxel claim,
 chunk allocation, scatter) with the batches already resident in HBM. The
-default workload is the 50M-point aerial scan in 1M-point batches.
+default workload is the 300M-point clustered building scan, cut into batches
+of 1M-10M points in shuffled order, applied by one persistent launch per step.
+
+The default run (one GPU) adds the two forms built on the update to the same
+line: `batched` (the 100M-point mixed stream in uneven batches of 64k-8M
+points: the autotuned plan against the same batches one launch per step and
+through the plain per-kernel path) and `serving` (16 resident octrees served
+from Poisson request traces against a plain server, latency p50/p99 and
+throughput).
 
 Prints one JSON line (rank 0). With --impl reference the CPU oracle is timed
 instead, on a bounded sample of the same workload.
@@ -162,9 +170,22 @@ def cpu_baseline(workload, budget_s: float = 12.0):
                       f"oracle, {dt:.1f} s"}
 
 
+def workload_config(w, max_batch: int, world: int) -> dict:
+    """The `config` object of the JSON line: the workload, its cut and the
+    octree parameters (the same for both arms)."""
+    return {"workload": w.name, "batch_points": int(max_batch),
+            "batches_per_step": len(w.counts), "points_per_step": w.n_points,
+            "leaf_capacity": 50_000, "chunk_points": 1000, "grid": 128,
+            "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (%.0f MB of points)" % (w.n_points * 16 / 2**20)}
+
+
 def run_reference(args):
-    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    """Reference arm: the CPU oracle as it stands, on the host cores, on a
+    bounded sample of the same workload (its first batches, at least
+    --ref-points points) per step."""
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return 0
     # the serving trace's octrees are terrain / uniform / clustered streams;
@@ -174,9 +195,11 @@ def run_reference(args):
     w, root_log2 = workload
     import oracle
     cfg = oracle.Config.make(root_min=w.root_min, root_log2=root_log2)
-    nb = max(1, min(len(w.counts), args.ref_batches))
+    nb, pts = 0, 0
+    while nb < len(w.counts) and (nb == 0 or pts < args.ref_points):
+        pts += int(w.counts[nb])
+        nb += 1
     sample = list(w.batches())[:nb]
-    pts = sum(len(b) for b in sample)
 
     def step():
         inc = oracle.Incremental(cfg)
@@ -191,14 +214,17 @@ def run_reference(args):
         step()
     dt = time.perf_counter() - t0
     value = pts * args.steps / dt / 1e6
+    what = (f"first {nb} batches ({pts} points) of {w.name} per step, sequential incremental "
+            f"oracle on one host core")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": w.name, "batches_per_step": nb, "points_per_step": pts},
+            "config": workload_config(w, max(int(c) for c in w.counts), world),
+            "sample": {"batches_per_step": nb, "points_per_step": pts},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"first {nb} batches ({pts} points) of {w.name}"},
+                             "sample": what},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -241,6 +267,8 @@ def rank_workload(name: str, points, rank: int, morton: bool = False):
             w.points = synth.terrain(1 + 1000 * rank, w.n_points)
         elif name == "uniform":
             w.points = synth.uniform(1000 * rank, 1_000_000, w.n_points)
+        elif name == "clustered":
+            w = synth.clustered_workload(n=w.n_points, seed=2 + 1000 * rank)
     return w, root_log2
 
 
@@ -479,7 +507,8 @@ def run_ours(args):
     if args.workload == "mixed" or args.batched:
         best, tune_ms = tree.autotune(ptrs, counts)
         plan = tree.plan(ptrs, counts, merge_points=best.merge_points,
-                         blocks_per_sm=best.blocks_per_sm, use_graph=True)
+                         blocks_per_sm=best.blocks_per_sm, use_graph=True,
+                         variant=best.variant)
         params, graphed = plan.info()
         for _ in range(args.warmup):
             tree.reset()
@@ -517,12 +546,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": w.name, "batch_points": max_batch, "batches_per_step": len(ptrs),
-                   "points_per_step": n_points, "leaf_capacity": cfg.leaf_capacity,
-                   "chunk_points": cfg.chunk_points, "grid": 1 << cfg.grid_log2,
-                   "path": path,
-                   "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (%.0f MB of points)" % (n_points * 16 / 2**20)},
+        "config": workload_config(w, max_batch, world),
+        "path": path,
         "latency_ms": {"fused_p50": percentile(lat_f, 50), "fused_p99": percentile(lat_f, 99),
                        "plain_p50": percentile(lat_p, 50), "plain_p99": percentile(lat_p, 99),
                        "batches": len(lat_f)},
@@ -557,14 +582,129 @@ def run_ours(args):
         line["update_roofline"] = {"alg_bytes_per_point": b_alg / B, "roofline_mpts": b_roof,
                                    "frac": value / world / b_roof, "form": "batched"}
         line["update_counts"]["S_batched"] = bstats["spilled"]
+    tree.close()
+    del tree, dev_pts
+    torch.cuda.empty_cache()
+    forms = args.forms and args.workload == "clustered" and not args.morton
+    if forms and world == 1:
+        # the two forms built on the update, each on its own workload
+        line["batched"] = batched_form(args)
+        torch.cuda.empty_cache()
+        line["serving"] = serving_form(args)
+        torch.cuda.empty_cache()
+    elif forms:
+        line["forms"] = "the batched and serving forms are measured in the one-GPU run"
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline((w, root_log2), args.cpu_budget)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    tree.close()
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def batched_form(args) -> dict:
+    """The batched form on the 100M-point mixed stream (terrain and clustered
+    runs, batches log-uniform in 64k-8M points): the autotuned plan (merged
+    updates, one persistent launch, CUDA-graph replay) against the same
+    batches applied one update each in one persistent launch, and through the
+    plain per-kernel path; per-batch latency of the fused form (one launch per
+    batch) against the plain form."""
+    import torch
+
+    from paper_2310_03567_gb300 import simlod
+    w, root_log2 = make_workload("mixed", None)
+    dev = simlod.points_tensor(w.points)
+    ptrs = [dev.data_ptr() + int(o) * 16 for o in w.offsets]
+    counts = [int(c) for c in w.counts]
+    tree = make_octree(w, root_log2)
+    stream = tree.stream
+
+    def check(rc, what):
+        if rc != simlod.OK:
+            raise simlod.SimlodError(rc, what)
+
+    def timed(step, k):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / k
+
+    best, tune_ms = tree.autotune(ptrs, counts)
+    plan = tree.plan(ptrs, counts, merge_points=best.merge_points,
+                     blocks_per_sm=best.blocks_per_sm, use_graph=True,
+                     variant=best.variant)
+    params, graphed = plan.info()
+
+    def plan_step():
+        tree.reset()
+        check(plan.run(), "plan run")
+
+    def fused_step():
+        tree.reset()
+        check(tree.insert_many_ptrs(ptrs, counts), "insert_batches")
+
+    lat_p = []
+
+    def plain_step(lat=None):
+        tree.reset()
+        for ptr, cnt in zip(ptrs, counts):
+            if lat is not None:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            check(tree.insert_ptr(ptr, cnt), "insert_batch")
+            if lat is not None:
+                b.record(stream)
+                lat.append((a, b))
+
+    for _ in range(args.warmup):
+        plan_step()
+    check(tree.sync(), "batched warm-up")
+    updates = tree.stats()["batches"]
+    spilled = tree.stats()["spilled"]
+    plan_ms = timed(plan_step, args.steps)
+    check(tree.sync(), "batched steps")
+    plan.close()
+    for _ in range(args.warmup):
+        fused_step()
+    fused_ms = timed(fused_step, args.steps)
+    check(tree.sync(), "fused steps")
+    plain_step()
+    plain_ms = timed(lambda: plain_step(lat_p), 1)
+    check(tree.sync(), "plain pass")
+    # per-batch latency of the fused form: each batch its own launch
+    tree.reset()
+    lat_f = []
+    for ptr, cnt in zip(ptrs, counts):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        check(tree.insert_many_ptrs([ptr], [cnt]), "insert_batches")
+        b.record(stream)
+        lat_f.append((a, b))
+    check(tree.sync(), "latency (fused)")
+    torch.cuda.synchronize()
+    lf = [a.elapsed_time(b) for a, b in lat_f]
+    lp = [a.elapsed_time(b) for a, b in lat_p]
+    tree.close()
+    n = w.n_points
+    out = {"workload": w.name, "batches": len(counts), "batch_points": "log-uniform 64k-8M",
+           "value": n / (plan_ms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": plan_ms,
+           "params": params, "graph": graphed, "updates_per_step": updates,
+           "spilled_per_step": spilled, "autotune_best_ms": tune_ms,
+           "fused_unmerged": {"value": n / (fused_ms * 1e-3) / 1e6, "ms_per_step": fused_ms},
+           "plain": {"value": n / (plain_ms * 1e-3) / 1e6, "ms_per_step": plain_ms},
+           "latency_ms": {"fused_p50": percentile(lf, 50), "fused_p99": percentile(lf, 99),
+                          "plain_p50": percentile(lp, 50), "plain_p99": percentile(lp, 99)}}
+    out["vs_fused_unmerged"] = out["value"] / out["fused_unmerged"]["value"]
+    out["vs_plain"] = out["value"] / out["plain"]["value"]
+    return out
 
 
 def serving_setup(scale: float, seed: int = 4):
@@ -600,29 +740,29 @@ def serving_setup(scale: float, seed: int = 4):
     return streams, specs
 
 
-def run_serving(args):
+def serving_form(args, rank: int = 0) -> dict:
     """Serving form: requests (log-uniform 100k-5M points) arrive by a Poisson
-    process at ~70 % of the plain path's measured capacity; the same trace is
-    served by the serving form and by a plain server (one request per update,
-    one update at a time)."""
+    process at ~70 % of the plain path's measured capacity; the same traces
+    are served by the serving form and by a plain server (one request per
+    update, one update at a time). Latency percentiles pool the requests of
+    the measured traces (after one untimed warm-up trace); a saturated run
+    queues a whole trace at once."""
     import torch
 
     from paper_2310_03567_gb300 import serving, simlod
-    if not torch.cuda.is_available():
-        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
-    rank = int(os.environ.get("RANK", "0"))
-    simlod.load()
     streams, specs = serving_setup(args.serving_scale, seed=4 + rank)
     total = sum(int(s.shape[0]) for s in streams)
     # capacity of the plain path on this box: one octree, 1M-point requests
     k0 = max(range(len(streams)), key=lambda k: streams[k].shape[0])
-    cal = serving.Server([specs[k0]], hbm_budget=1 << 40, plain=True)
+    cal = serving.Server([specs[k0]], hbm_budget=1 << 40, plain=True, staging_cap=1 << 30)
     n_cal = min(int(streams[k0].shape[0]), 20_000_000)
     cal_reqs = [serving.Request(0, streams[k0][o:o + 1_000_000], 0.0)
                 for o in range(0, n_cal, 1_000_000)]
     cal.run(cal_reqs)
     cap = cal.report()["mpts_per_s"] * 1e6
     cal.close()
+    del cal
+    torch.cuda.empty_cache()
     rate = 0.7 * cap
     # several independent Poisson traces (each the whole stream of every
     # octree); latency percentiles pool their requests, since a p99 over one
@@ -633,29 +773,31 @@ def run_serving(args):
     arenas = sum(simlod.arena_bytes(sp.cfg, sp.data_bytes) for sp in specs)
     budget = arenas + (4 << 30)
     out = {}
+    clk = None
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     for name, plain in (("serving", False), ("plain", True)):
         lat, wait, reps = [], [], []
-        # an untimed warm-up run of the first trace, then the measured traces
+        srv = serving.Server(specs, hbm_budget=budget, compute_slots=2, frame_ms=33.3,
+                             plain=plain)
+        # an untimed warm-up run of the first trace, then the measured traces,
+        # all on the same resident octrees (reset between traces)
         for t, tr in enumerate([traces[0]] + traces):
             for r in tr:
-                r.admitted = r.done = -1.0
-            srv = serving.Server(specs, hbm_budget=budget, compute_slots=2, frame_ms=33.3,
-                                 plain=plain)
+                r.admitted = r.launched = r.done = -1.0
+            srv.reset()
             if not plain and t == 1:
                 clocks.start()
             done = srv.run(tr)
             if not plain and t == 1:
                 clk = clocks.stop()
             if t == 0:
-                srv.close()
-                torch.cuda.empty_cache()
                 continue
             lat += [(r.done - r.arrival) * 1e3 for r in done]
             wait += [(r.admitted - r.arrival) * 1e3 for r in done]
             reps.append(srv.report())
-            srv.close()
-            torch.cuda.empty_cache()
+        srv.close()
+        del srv
+        torch.cuda.empty_cache()
         rep = dict(reps[0])
         rep["traces"] = len(traces)
         rep["requests"] = len(lat)
@@ -670,7 +812,7 @@ def run_serving(args):
     sat = {}
     for name, plain in (("serving", False), ("plain", True)):
         for r in reqs:
-            r.admitted = r.done = -1.0
+            r.admitted = r.launched = r.done = -1.0
             r.arrival = 0.0
         srv = serving.Server(specs, hbm_budget=budget, compute_slots=2, frame_ms=33.3,
                              plain=plain)
@@ -679,30 +821,54 @@ def run_serving(args):
         sat[name] = {"mpts_per_s": rep["mpts_per_s"], "seconds": rep["seconds"],
                      "launches": rep["launches"], "frames": rep["frames"]}
         srv.close()
+        del srv
         torch.cuda.empty_cache()
     sat["serving_vs_plain"] = sat["serving"]["mpts_per_s"] / sat["plain"]["mpts_per_s"]
     sv, pl = out["serving"], out["plain"]
-    line = {
-        "metric": METRIC, "value": sv["mpts_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
-        "warmup": 0, "ms_per_step": sv["seconds"] * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": f"serving-16 octrees ({total} points, scale {args.serving_scale})",
-                   "requests": len(reqs), "traces": len(traces),
-                   "request_points": "log-uniform 100k-5M",
-                   "arrival": f"Poisson, {rate / 1e6:.0f} Mpts/s (70% of plain capacity "
-                              f"{cap / 1e6:.0f} Mpts/s)",
-                   "hbm_budget_bytes": budget, "frame": "1920x1080 render of every octree "
-                                                        "every 33.3 ms",
-                   "path": "serving form: HBM-budget admission, continuous batching, "
-                           "2 half-GPU persistent launches in flight",
-                   "inputs": "pinned host memory (copies inside the served latency)"},
+    return {
+        "workload": f"serving-16 octrees ({total} points, scale {args.serving_scale} of "
+                    f"5M-200M points each)",
+        "value": sv["mpts_per_s"], "unit": UNIT,
+        "requests": len(reqs), "traces": len(traces), "request_points": "log-uniform 100k-5M",
+        "arrival": f"Poisson, {rate / 1e6:.0f} Mpts/s (70% of plain capacity "
+                   f"{cap / 1e6:.0f} Mpts/s)",
+        "hbm_budget_bytes": budget,
+        "frame": "1920x1080 render of every octree every 33.3 ms",
+        "path": "serving form: HBM-budget admission, continuous batching, "
+                "2 half-GPU persistent launches in flight",
+        "inputs": "pinned host memory (copies inside the served latency)",
         "latency_ms": {"serving_p50": sv["latency_ms"]["p50"],
                        "serving_p99": sv["latency_ms"]["p99"],
                        "plain_p50": pl["latency_ms"]["p50"], "plain_p99": pl["latency_ms"]["p99"]},
         "serving": sv, "plain": pl, "saturated": sat,
-        "e2e": {"value": sv["mpts_per_s"], "unit": UNIT,
-                "h2d_bytes_per_step": 16 * total, "d2h_bytes_per_step": 0},
-        "gpu_launches": sv["launches"], "clocks": clk,
+        "h2d_bytes_per_trace": 16 * total, "gpu_launches": sv["launches"], "clocks": clk,
+    }
+
+
+def run_serving(args):
+    """The serving form alone, as its own JSON line."""
+    import torch
+
+    from paper_2310_03567_gb300 import simlod
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    rank = int(os.environ.get("RANK", "0"))
+    simlod.load()
+    f = serving_form(args, rank)
+    sv = f["serving"]
+    line = {
+        "metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": sv["seconds"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f["workload"], "requests": f["requests"],
+                   "traces": f["traces"], "request_points": f["request_points"],
+                   "arrival": f["arrival"], "hbm_budget_bytes": f["hbm_budget_bytes"],
+                   "frame": f["frame"], "path": f["path"], "inputs": f["inputs"]},
+        "latency_ms": f["latency_ms"], "serving": sv, "plain": f["plain"],
+        "saturated": f["saturated"],
+        "e2e": {"value": f["value"], "unit": UNIT,
+                "h2d_bytes_per_step": f["h2d_bytes_per_trace"], "d2h_bytes_per_step": 0},
+        "gpu_launches": f["gpu_launches"], "clocks": f["clocks"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -782,14 +948,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="aerial",
+    ap.add_argument("--workload", default="clustered",
                     choices=["aerial", "uniform", "clustered", "mixed", "serving"])
     ap.add_argument("--serving-traces", type=int, default=3,
                     help="independent Poisson traces whose requests the serving latency pools")
-    ap.add_argument("--serving-scale", type=float, default=0.25,
+    ap.add_argument("--serving-scale", type=float, default=1.0,
                     help="octree sizes of the serving workload relative to 5M-200M points")
+    ap.add_argument("--no-forms", dest="forms", action="store_false",
+                    help="skip the batched and serving sub-measurements of the default run")
     ap.add_argument("--points", type=int, default=None)
-    ap.add_argument("--ref-batches", type=int, default=2)
+    ap.add_argument("--ref-points", type=int, default=1_000_000,
+                    help="reference arm: the first batches of the workload up to at least this "
+                         "many points, per step")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--chunk-sweep", action="store_true",

@@ -244,9 +244,9 @@ SIMLOD_API int simlod_insert_batches_host(simlod_t* h, const simlod_point* const
 typedef struct simlod_plan simlod_plan_t;
 typedef struct {
   uint64_t merge_points;  /* merged update size; 0 = one update per batch; at most max_batch_points */
-  uint32_t blocks_per_sm; /* persistent blocks (512 threads) per SM: 1, 2, or 0 = as many as fit */
+  uint32_t blocks_per_sm; /* persistent blocks per SM: 1 .. the kernel instance's maximum, 0 = all that fit */
   uint32_t use_graph;     /* capture the run in a CUDA graph */
-  uint32_t reserved;
+  uint32_t variant;       /* kernel instance, 0 .. SIMLOD_N_VARIANTS - 1 (simlod_variant_info) */
 } simlod_plan_params;
 SIMLOD_API int simlod_plan_create(simlod_t* h, const simlod_point* const* d_batches,
                                   const uint64_t* counts, uint32_t n_batches,
@@ -257,14 +257,37 @@ SIMLOD_API int simlod_plan_run(simlod_plan_t* plan, void* stream);
 SIMLOD_API int simlod_plan_info(const simlod_plan_t* plan, simlod_plan_params* params,
                                 uint32_t* graphed);
 SIMLOD_API int simlod_plan_destroy(simlod_plan_t* plan);
-/* Autotuner of the batched form: times plans for this batch list over merge
- * sizes (none, 256k, 1M, 2M, 4M, 8M points, max_batch_points; those below
- * max_batch_points) and 1 or 2 blocks per SM, on `h` itself (reset before
- * every trial and at the end: pass a scratch handle of the same configuration
- * to keep an octree), and returns the fastest parameters and their time. */
+/* Autotuner of the batched form (Section 4's persistent update kernel, with
+ * its block and tile parameters chosen per workload): times plans for this
+ * batch list on `h` itself (reset before every trial and at the end: pass a
+ * scratch handle of the same configuration to keep an octree). First every
+ * kernel instance (simlod_variant_info) at its largest and half its largest
+ * blocks per SM, with updates merged up to max_batch_points; then, for the
+ * fastest of those, every merge size (none, 256k, 1M, 2M, 4M, 8M points,
+ * max_batch_points; those below max_batch_points). Returns the fastest
+ * parameters and their time. The choice is kept per device, configuration
+ * and batch list (counts): a later call with the same ones returns it at
+ * once without timing anything (best_ms then holds the time measured when
+ * it was chosen). */
 SIMLOD_API int simlod_plan_autotune(simlod_t* h, const simlod_point* const* d_batches,
                                     const uint64_t* counts, uint32_t n_batches, void* stream,
                                     simlod_plan_params* best, double* best_ms);
+
+/* Kernel instances of the batched form: the same persistent update kernel
+ * compiled with other block and tile parameters. */
+#define SIMLOD_N_VARIANTS 4
+typedef struct {
+  uint32_t threads_per_block;
+  uint32_t max_blocks_per_sm;  /* that fit on the current device */
+  uint32_t node_cache;         /* node-table entries mirrored in shared memory */
+  uint32_t store_unroll;       /* records per thread in flight while storing */
+  uint32_t descent_group;      /* tree levels whose occupancy words load together */
+  uint32_t smem_bytes;         /* dynamic shared memory per block */
+} simlod_variant_desc;
+/* Parameters of kernel instance `variant` on the current device;
+ * SIMLOD_ERR_INVALID_ARG for an unknown instance, SIMLOD_ERR_CUDA when the
+ * device cannot run it. */
+SIMLOD_API int simlod_variant_info(uint32_t variant, simlod_variant_desc* out);
 
 /* Width of the handle's persistent launches (simlod_insert_batches,
  * simlod_frame_update): blocks_per_sm blocks of 512 threads per SM, from 1 to
@@ -276,6 +299,16 @@ SIMLOD_API int simlod_plan_autotune(simlod_t* h, const simlod_point* const* d_ba
  * until their barriers time out (SIMLOD_ERR_TIMEOUT). */
 SIMLOD_API int simlod_set_launch_width(simlod_t* h, uint32_t blocks_per_sm,
                                        uint32_t* max_blocks_per_sm);
+
+/* Time limits of the waits inside the handle's persistent launches (not in
+ * the paper, whose kernel waits without a limit): barrier_ns bounds one
+ * block's wait at a grid barrier, ready_ns one wait for a batch's ready flag
+ * (simlod_insert_batches_host); 0 restores the default of 2 s. A wait that
+ * runs out aborts the launch: every block leaves at its next barrier,
+ * simlod_sync returns SIMLOD_ERR_TIMEOUT, the handle is poisoned and
+ * simlod_reset makes it usable again. The limits apply to launches enqueued
+ * after the call (a plan keeps the limits it was created with). */
+SIMLOD_API int simlod_set_wait_limits(simlod_t* h, uint64_t barrier_ns, uint64_t ready_ns);
 
 /* Frame-budget update (Section 7.2): as simlod_insert_batches, but before
  * starting batch k > 0 the kernel checks the time since the launch began
@@ -368,12 +401,15 @@ SIMLOD_API int simlod_get_timing(simlod_t* h, simlod_timing* out);
  * Scratch lives in one fixed array of about 4.5 MiB per device, a file-scope
  * device variable that every GPU loading this library holds until the
  * process exits; hence n is limited to SIMLOD_NOALLOC_MAX_POINTS and larger
- * batches are rejected with SIMLOD_ERR_INVALID_ARG. The first call on a device
- * looks up that array's device address with the device current; make that
- * first call before any stream capture. Every call clears and reuses the same
- * array, so calls whose work overlaps on the GPU (different streams, other
- * threads) race and must be serialised by the caller. Calls no cudaMalloc,
- * cudaFree or allocating library routine. */
+ * batches are rejected with SIMLOD_ERR_INVALID_ARG. Every call looks up that
+ * array's device address in the current context (a host-side query; the
+ * first call in a context also loads the library's device code, so make that
+ * first call before any stream capture). Every call clears and reuses the
+ * same array, so calls whose work overlaps on the GPU (different streams,
+ * other threads) race and must be serialised by the caller. Calls no
+ * cudaMalloc, cudaFree or allocating library routine. An error already
+ * pending in the CUDA runtime from earlier work is reported as
+ * SIMLOD_ERR_CUDA and left in place for the caller to read. */
 SIMLOD_API int simlod_sample_node_noalloc(const simlod_point* d_pts, uint64_t n,
                                           const int32_t node_min[3], uint32_t log2size,
                                           uint32_t grid_log2, simlod_voxel_rec* d_voxels,

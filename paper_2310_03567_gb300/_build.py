@@ -2,14 +2,18 @@
 
 Compiles the CUDA library (``libsimlod.so``, sm_103a only) and the seeded
 input generator (``synth/libsynth.so``). Both land next to their sources and
-are rebuilt only when a source or header is newer than the built file.
+are rebuilt only when a source or header is newer than the built file. The
+library's translation units compile in parallel into objects under
+``build/<machine>/`` and are then linked.
 """
 from __future__ import annotations
 
 import glob
 import os
+import platform
 import shutil
 import subprocess
+from concurrent.futures import ThreadPoolExecutor
 
 PKG_DIR = os.path.dirname(os.path.abspath(__file__))
 REPO_DIR = os.path.dirname(PKG_DIR)
@@ -20,6 +24,18 @@ SYNTH_DIR = os.path.join(PKG_DIR, "synth")
 SYNTH_LIB = os.path.join(SYNTH_DIR, "libsynth.so")
 
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
+OBJ_DIR = os.path.join(PKG_DIR, "build", platform.machine())
+
+# Instances of the persistent update kernel beyond the one built into
+# simlod.cu (instance 0: 512 threads, 2 blocks per SM, 4,096 cached nodes,
+# store unroll 2, descent group 2), each built from fused_variant.cu:
+# (threads per block, blocks per SM, node-cache entries, store unroll,
+# descent group). The batched form's autotuner picks among all of them.
+VARIANTS = [
+    (256, 4, 2048, 2, 2),
+    (1024, 1, 8192, 2, 2),
+    (512, 2, 4096, 1, 2),
+]
 
 
 def _nvcc() -> str:
@@ -43,35 +59,70 @@ def _run(cmd: list[str]) -> None:
 
 
 def library_sources() -> list[str]:
-    return sorted(glob.glob(os.path.join(CSRC_DIR, "*.cu")))
+    return sorted(f for f in glob.glob(os.path.join(CSRC_DIR, "*.cu"))
+                  if os.path.basename(f) != "fused_variant.cu")
 
 
 def library_headers() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC_DIR, "*.cuh")) +
+                  glob.glob(os.path.join(CSRC_DIR, "*.h")) +
                   glob.glob(os.path.join(INCLUDE_DIR, "*.h")))
 
 
-def library_command(out: str = LIB_PATH, extra: list[str] | None = None) -> list[str]:
+def _common_flags(extra: list[str] | None = None) -> list[str]:
     # -dlcm=cg: plain global loads are served by the coherent L2, not the
     # per-SM L1, because the persistent kernel re-reads node tables, split
     # lists and grids that other blocks rewrote after a grid barrier (L1s are
     # not coherent with each other within one grid). Batch points are read
     # with __ldcg too: a merged update reads them from a staging buffer that
     # the same launch has just written.
-    return ([_nvcc(), *ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17", "-shared",
-             "-Xptxas", "-dlcm=cg",
+    return ([*ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17", "-Xptxas", "-dlcm=cg",
              "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-             "-I", INCLUDE_DIR, "-I", CSRC_DIR]
-            + (extra or []) + library_sources() + ["-o", out])
+             "-I", INCLUDE_DIR, "-I", CSRC_DIR] + (extra or []))
 
 
-def build_library(force: bool = False) -> str:
-    srcs = library_sources() + library_headers() + [os.path.abspath(__file__)]
-    if force or _stale(LIB_PATH, srcs):
-        tmp = LIB_PATH + ".tmp"
-        _run(library_command(tmp))
-        os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+def variant_flags(k: int) -> list[str]:
+    """Defines of kernel instance k >= 1 (fused_variant.cu)."""
+    block, per_sm, cache, store_u, group = VARIANTS[k - 1]
+    return [f"-DSL_NS=sl_v{k}", f"-DSL_VARIANT_INFO=sl_fused_variant_info_{k}",
+            f"-DSL_VARIANT_LAUNCH=sl_fused_variant_launch_{k}",
+            f"-DSL_PHASE_BLOCK={block}", f"-DSL_PHASE_MIN_BLOCKS={per_sm}",
+            f"-DSL_NODE_CACHE={cache}", f"-DSL_STORE_UNROLL={store_u}",
+            f"-DSL_DESCENT_GROUP={group}"]
+
+
+def compile_commands(extra: list[str] | None = None, obj_dir: str = OBJ_DIR):
+    """(command, object) for every translation unit of the library."""
+    cmds = []
+    for src in library_sources():
+        obj = os.path.join(obj_dir, os.path.basename(src)[:-3] + ".o")
+        cmds.append(([_nvcc(), *_common_flags(extra), "-c", src, "-o", obj], obj))
+    vsrc = os.path.join(CSRC_DIR, "fused_variant.cu")
+    for k in range(1, len(VARIANTS) + 1):
+        obj = os.path.join(obj_dir, f"fused_variant_{k}.o")
+        cmds.append(([_nvcc(), *_common_flags((extra or []) + variant_flags(k)), "-c", vsrc,
+                      "-o", obj], obj))
+    return cmds
+
+
+def link_command(objs: list[str], out: str) -> list[str]:
+    return [_nvcc(), *ARCH_FLAGS, "-shared", "-Xcompiler", "-fPIC", *objs, "-o", out]
+
+
+def build_library(force: bool = False, out: str = LIB_PATH, extra: list[str] | None = None,
+                  obj_dir: str = OBJ_DIR) -> str:
+    srcs = (library_sources() + [os.path.join(CSRC_DIR, "fused_variant.cu")] +
+            library_headers() + [os.path.abspath(__file__)])
+    if force or _stale(out, srcs):
+        os.makedirs(obj_dir, exist_ok=True)
+        cmds = compile_commands(extra, obj_dir)
+        with ThreadPoolExecutor(len(cmds)) as ex:
+            for f in [ex.submit(_run, c) for c, _ in cmds]:
+                f.result()
+        tmp = out + ".tmp"
+        _run(link_command([o for _, o in cmds], tmp))
+        os.replace(tmp, out)
+    return out
 
 
 def build_synth(force: bool = False) -> str:

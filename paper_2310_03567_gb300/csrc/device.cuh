@@ -44,7 +44,14 @@
 
 #include "simlod.h"
 
-namespace sl {
+// Namespace of this instance of the device code: the library builds the
+// persistent update kernel more than once, with other launch-shape knobs,
+// each instance in a namespace of its own (fused_variant.cu).
+#ifndef SL_NS
+#define SL_NS sl
+#endif
+
+namespace SL_NS {
 
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr unsigned long long HASH_EMPTY = ~0ull;
@@ -224,6 +231,8 @@ struct Ctx {
   uint64_t max_batch;
   uint64_t mv_cap;  // entries of each mover list (batch + spill capacity)
   unsigned long long* launch_bar;  // barrier word of the persistent launch (abort bit)
+  unsigned long long bar_ns;       // persistent launch: time limit of one grid-barrier wait
+  unsigned long long ready_ns;     //   and of one wait for a batch's ready flag
 };
 
 // Abort bit of a persistent launch's barrier word: set with the first
@@ -1532,4 +1541,4 @@ __device__ void phase_end_rejected(const Ctx& c) {
   t->st_rejected += 1;
 }
 
-}  // namespace sl
+}  // namespace SL_NS

@@ -5,18 +5,19 @@
 // the update kernel looping over the batches uploaded so far), with the
 // phases of device.cuh.
 //
-// Barriers are bounded: a block that waits longer than FUSED_BARRIER_NS
-// marks the launch aborted and returns, the others see the abort flag (or
-// time out themselves) and return as well; the host then reads a TIMEOUT
-// status. Nothing spins without a limit.
+// Barriers are bounded: a block that waits longer than the handle's barrier
+// limit (Ctx::bar_ns, 2 s unless the caller sets another) marks the launch
+// aborted and returns, the others see the abort flag (or time out themselves)
+// and return as well; the host then reads a TIMEOUT status. Nothing spins
+// without a limit.
 #pragma once
 
 #include "device.cuh"
 
-namespace sl {
+namespace SL_NS {
 
-constexpr unsigned long long FUSED_BARRIER_NS = 2000000000ull;  // 2 s
-constexpr unsigned long long FUSED_READY_NS = 2000000000ull;    // 2 s per batch
+constexpr unsigned long long FUSED_BARRIER_NS = 2000000000ull;  // default barrier limit: 2 s
+constexpr unsigned long long FUSED_READY_NS = 2000000000ull;    // default ready limit: 2 s per batch
 constexpr int FUSED_BLOCK = PHASE_BLOCK;
 constexpr unsigned long long NO_BUDGET = ~0ull;
 constexpr uint32_t MAX_FUSED_BATCHES = 16384;
@@ -86,7 +87,7 @@ __device__ __forceinline__ bool grid_barrier(const Ctx& c, FusedCtl* f) {
           break;
         }
         if (v >= target) break;
-        if ((k & 15u) == 0u && globaltimer_ns() - t0 > FUSED_BARRIER_NS) {
+        if ((k & 15u) == 0u && globaltimer_ns() - t0 > c.bar_ns) {
           set_error(c, E_TIMEOUT);  // also sets the abort bit
           ok = 0;
           break;
@@ -104,7 +105,7 @@ __device__ __forceinline__ bool grid_barrier(const Ctx& c, FusedCtl* f) {
 // Wait until a batch is ready: *flag != 0, written by a copy on another
 // stream after the batch's own copy (Section 4: the update kernel handles the
 // batches uploaded so far). Thread 0 of each block polls, bounded by
-// FUSED_READY_NS; the abort bit ends the wait too. Returns false when the
+// Ctx::ready_ns; the abort bit ends the wait too. Returns false when the
 // launch was aborted.
 __device__ __forceinline__ bool wait_ready(const Ctx& c, FusedCtl* f, const unsigned int* flag) {
   __shared__ int s_ok;
@@ -122,7 +123,7 @@ __device__ __forceinline__ bool wait_ready(const Ctx& c, FusedCtl* f, const unsi
           ok = 0;
           break;
         }
-        if ((k & 15u) == 0u && globaltimer_ns() - t0 > FUSED_READY_NS) {
+        if ((k & 15u) == 0u && globaltimer_ns() - t0 > c.ready_ns) {
           set_error(c, E_TIMEOUT);
           ok = 0;
           break;
@@ -343,4 +344,4 @@ __global__ void k_plan_groups(Ctx c, const PlanInput* in, uint32_t n_in, const u
   }
 }
 
-}  // namespace sl
+}  // namespace SL_NS

@@ -14,7 +14,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "simlod.h"
 
@@ -61,22 +60,16 @@ struct NaScratch {
 // 4 MiB + 512 KiB + 256 B per device, for the life of the process.
 static __device__ __align__(256) NaScratch g_na_scratch;
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_na_mutex;
-NaScratch* g_na_ptr[MAX_DEVICES] = {};
-
-// Device address of g_na_scratch on the current device (looked up once per
-// device; in host code the symbol itself is only a stand-in).
+// Device address of g_na_scratch in the current context. In host code the
+// symbol itself is only a stand-in, not a device address. The address is
+// looked up on every call (a host-side query, no stream work): a context
+// re-created on the device (after cudaDeviceReset) reloads this module, and
+// the array may then sit elsewhere. The first call in a context also loads
+// the module's device code.
 int na_scratch(NaScratch** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return SIMLOD_ERR_CUDA;
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) return SIMLOD_ERR_CUDA;
-    g_na_ptr[dev] = static_cast<NaScratch*>(p);
-  }
-  *out = g_na_ptr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) return SIMLOD_ERR_CUDA;
+  *out = static_cast<NaScratch*>(p);
   return SIMLOD_OK;
 }
 
@@ -176,17 +169,23 @@ extern "C" SIMLOD_API int simlod_sample_node_noalloc(const simlod_point* d_pts, 
   if (voxels_capacity < (n < cells ? n : cells)) return SIMLOD_ERR_INVALID_ARG;
   for (int a = 0; a < 3; ++a)
     if ((long long)node_min[a] + (1ll << log2size) - 1 > 0x7FFFFFFFll) return SIMLOD_ERR_INVALID_ARG;
+  // an error already pending from earlier work is reported, not cleared
+  if (cudaPeekAtLastError() != cudaSuccess) return SIMLOD_ERR_CUDA;
   NaScratch* s = nullptr;
   int rc = na_scratch(&s);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int3 mn = make_int3(node_min[0], node_min[1], node_min[2]);
+  // the whole table is cleared on every call: a table left by a context that
+  // no longer exists, or by a call that failed half way, may hold anything
   k_na_clear<<<256, 256, 0, st>>>(s);
+  if (cudaPeekAtLastError() != cudaSuccess) return SIMLOD_ERR_CUDA;
   if (n) {
     const uint32_t blocks = (uint32_t)((n + 255) / 256);
     k_na_claim<<<blocks, 256, 0, st>>>(s, reinterpret_cast<const int4*>(d_pts), (uint32_t)n, mn,
                                        log2size, grid_log2);
+    if (cudaPeekAtLastError() != cudaSuccess) return SIMLOD_ERR_CUDA;
   }
   k_na_emit<<<64, 256, 0, st>>>(s, mn, log2size, grid_log2, d_voxels, d_count);
-  return cudaGetLastError() == cudaSuccess ? SIMLOD_OK : SIMLOD_ERR_CUDA;
+  return cudaPeekAtLastError() == cudaSuccess ? SIMLOD_OK : SIMLOD_ERR_CUDA;
 }

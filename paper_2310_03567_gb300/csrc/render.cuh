@@ -23,7 +23,7 @@
 
 #include "device.cuh"
 
-namespace sl {
+namespace SL_NS {
 
 struct View {
   float m[16];
@@ -164,4 +164,4 @@ __global__ void k_fb_clear(unsigned long long* fb, uint64_t n) {
     fb[i] = ~0ull;
 }
 
-}  // namespace sl
+}  // namespace SL_NS

@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -12,6 +14,7 @@
 #include "fused.cuh"
 #include "render.cuh"
 #include "simlod.h"
+#include "variant.h"
 
 using namespace sl;
 
@@ -103,6 +106,70 @@ __global__ void k_end(Ctx c, uint64_t n, uint32_t iters) { phase_end(c, n, iters
 
 __global__ void k_end_rejected(Ctx c) { phase_end_rejected(c); }
 
+// Kernel instance 0: the k_fused of this file (the header's knobs).
+int fused_info_0(sl_variant_info* out) {
+  out->block = FUSED_BLOCK;
+  out->min_blocks = PHASE_MIN_BLOCKS;
+  out->node_cache = NODE_CACHE;
+  out->store_unroll = STORE_U;
+  out->descent_group = DESCENT_GROUP;
+  out->smem_bytes = PHASE_SMEM_BYTES;
+  out->max_per_sm = 0;
+  if (cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           PHASE_SMEM_BYTES) != cudaSuccess)
+    return 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused, FUSED_BLOCK,
+                                                    PHASE_SMEM_BYTES) != cudaSuccess)
+    return 1;
+  out->max_per_sm = n;
+  return 0;
+}
+
+int fused_launch_0(const sl_fused_launch* a) {
+  if (a->ctx_bytes != sizeof(Ctx)) return (int)cudaErrorInvalidValue;
+  Ctx c;
+  memcpy(&c, a->ctx, sizeof(Ctx));
+  const BatchDesc* bt = static_cast<const BatchDesc*>(a->batches);
+  uint32_t n = a->n_batches;
+  FusedCtl* f = static_cast<FusedCtl*>(a->fctl);
+  unsigned long long budget = a->budget_ns;
+  uint32_t max_iters = a->max_iters;
+  const unsigned int* n_dev = a->n_dev;
+  const PlanSeg* segs = static_cast<const PlanSeg*>(a->segs);
+  const unsigned int* ready = a->ready;
+  void* args[] = {&c, &bt, &n, &f, &budget, &max_iters, &n_dev, &segs, &ready};
+  return (int)cudaLaunchCooperativeKernel((const void*)k_fused, dim3(a->grid), dim3(FUSED_BLOCK),
+                                          args, PHASE_SMEM_BYTES,
+                                          static_cast<cudaStream_t>(a->stream));
+}
+
+}  // namespace
+
+// The other kernel instances (fused_variant.cu, one object per instance).
+extern "C" {
+int sl_fused_variant_info_1(sl_variant_info* out);
+int sl_fused_variant_launch_1(const sl_fused_launch* a);
+int sl_fused_variant_info_2(sl_variant_info* out);
+int sl_fused_variant_launch_2(const sl_fused_launch* a);
+int sl_fused_variant_info_3(sl_variant_info* out);
+int sl_fused_variant_launch_3(const sl_fused_launch* a);
+}
+
+namespace {
+
+struct VariantFns {
+  int (*info)(sl_variant_info*);
+  int (*launch)(const sl_fused_launch*);
+};
+static_assert(SL_N_VARIANTS == SIMLOD_N_VARIANTS, "kernel instances");
+const VariantFns kVariants[SL_N_VARIANTS] = {
+    {fused_info_0, fused_launch_0},
+    {sl_fused_variant_info_1, sl_fused_variant_launch_1},
+    {sl_fused_variant_info_2, sl_fused_variant_launch_2},
+    {sl_fused_variant_info_3, sl_fused_variant_launch_3},
+};
+
 }  // namespace
 
 // ================================================================ host side
@@ -132,6 +199,7 @@ struct simlod {
   // fused form
   int fused_grid;           // blocks of k_fused launches
   int fused_max_per_sm;     // co-resident k_fused blocks per SM
+  sl_variant_info var[SL_N_VARIANTS];  // kernel instances of the batched form
   bool mirror_stale;        // a fused launch ran since the last control-block read
   unsigned long long rejected_async_seen;  // fused-launch rejections already reported
   BatchDesc* desc_host;     // pinned staging of the batch table
@@ -303,6 +371,8 @@ void make_ctx(simlod_t* h) {
   c.max_splits = (uint32_t)L.max_splits;
   c.max_batch = g.max_batch_points;
   c.mv_cap = g.max_batch_points + g.spill_capacity;
+  c.bar_ns = FUSED_BARRIER_NS;
+  c.ready_ns = FUSED_READY_NS;
 }
 
 int error_from_bits(uint32_t e) {
@@ -626,6 +696,11 @@ SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t are
     h->fused_max_per_sm = std::min(bpsm, 4);
     h->fused_grid = h->fused_max_per_sm * h->sm_count;
   }
+  for (int k = 0; k < SL_N_VARIANTS; ++k) {
+    if (kVariants[k].info(&h->var[k]) != 0) h->var[k].max_per_sm = 0;
+    if (!coop) h->var[k].max_per_sm = 0;
+  }
+  cudaGetLastError();  // an instance this device cannot run is simply never used
   if (cudaMallocHost(reinterpret_cast<void**>(&h->desc_host),
                      sizeof(BatchDesc) * MAX_FUSED_BATCHES) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&h->fctl_host), sizeof(FusedCtl)) != cudaSuccess ||
@@ -782,18 +857,20 @@ int plan_enqueue(simlod_plan_t* P, cudaStream_t s) {
   if (cudaGetLastError() != cudaSuccess ||
       cudaMemsetAsync(h->fctl_dev, 0, sizeof(FusedCtl), s) != cudaSuccess)
     return SIMLOD_ERR_CUDA;
-  const BatchDesc* bt = P->groups;
-  uint32_t n = P->n;
-  FusedCtl* f = h->fctl_dev;
-  unsigned long long budget = NO_BUDGET;
-  uint32_t max_iters = h->cfg.max_expand_iters ? h->cfg.max_expand_iters : h->cfg.root_log2 + 1;
-  const unsigned int* n_dev = P->n_groups;
-  const PlanSeg* segs = P->segs;
-  const unsigned int* ready = nullptr;
-  void* args[] = {&c, &bt, &n, &f, &budget, &max_iters, &n_dev, &segs, &ready};
-  if (cudaLaunchCooperativeKernel((const void*)k_fused, dim3(P->grid), dim3(FUSED_BLOCK), args,
-                                  PHASE_SMEM_BYTES, s) != cudaSuccess)
-    return SIMLOD_ERR_CUDA;
+  sl_fused_launch a;
+  a.ctx = &c;
+  a.ctx_bytes = sizeof(Ctx);
+  a.batches = P->groups;
+  a.n_batches = P->n;
+  a.fctl = h->fctl_dev;
+  a.budget_ns = NO_BUDGET;
+  a.max_iters = h->cfg.max_expand_iters ? h->cfg.max_expand_iters : h->cfg.root_log2 + 1;
+  a.n_dev = P->n_groups;
+  a.segs = P->segs;
+  a.ready = nullptr;
+  a.grid = P->grid;
+  a.stream = s;
+  if (kVariants[P->p.variant].launch(&a) != (int)cudaSuccess) return SIMLOD_ERR_CUDA;
   return SIMLOD_OK;
 }
 
@@ -803,11 +880,13 @@ SIMLOD_API int simlod_plan_create(simlod_t* h, const simlod_point* const* d_batc
                                   const uint64_t* counts, uint32_t n_batches,
                                   const simlod_plan_params* params, simlod_plan_t** out) {
   if (!h || !out || !params || (n_batches && (!d_batches || !counts)) ||
-      n_batches > MAX_FUSED_BATCHES || params->blocks_per_sm > 2)
+      n_batches > MAX_FUSED_BATCHES || params->variant >= SL_N_VARIANTS)
     return SIMLOD_ERR_INVALID_ARG;
   *out = nullptr;
+  const int vmax = h->var[params->variant].max_per_sm;
+  if (params->blocks_per_sm > (uint32_t)std::max(vmax, 0)) return SIMLOD_ERR_INVALID_ARG;
   if (h->sticky) return SIMLOD_ERR_POISONED;
-  if (h->fused_grid < 1) return SIMLOD_ERR_CUDA;
+  if (vmax < 1) return SIMLOD_ERR_CUDA;
   uint64_t total = 0;
   std::vector<PlanInput> in(n_batches);
   std::vector<uint32_t> tile0(n_batches + 1, 0);
@@ -826,9 +905,8 @@ SIMLOD_API int simlod_plan_create(simlod_t* h, const simlod_point* const* d_batc
   P->n = n_batches;
   P->total = total;
   P->units = tile0[n_batches];
-  const unsigned per_sm = (unsigned)h->fused_max_per_sm;
   P->grid = (unsigned)h->sm_count *
-            (params->blocks_per_sm ? std::min<unsigned>(params->blocks_per_sm, per_sm) : per_sm);
+            (params->blocks_per_sm ? params->blocks_per_sm : (unsigned)vmax);
   P->last = h->last_stream;
   const size_t nb = std::max<uint32_t>(n_batches, 1);
   size_t o = 0;
@@ -918,49 +996,118 @@ SIMLOD_API int simlod_plan_destroy(simlod_plan_t* P) {
   return SIMLOD_OK;
 }
 
+namespace {
+
+// Autotuner choices, per device, configuration and batch list.
+struct TuneKey {
+  int device, sm_count;
+  std::vector<uint64_t> words;  // configuration fields and the batch counts
+  bool operator<(const TuneKey& o) const {
+    if (device != o.device) return device < o.device;
+    if (sm_count != o.sm_count) return sm_count < o.sm_count;
+    return words < o.words;
+  }
+};
+struct TuneChoice {
+  simlod_plan_params p;
+  double ms;
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneChoice> g_tune_cache;
+
+TuneKey tune_key(const simlod_t* h, const uint64_t* counts, uint32_t n) {
+  TuneKey k;
+  k.device = 0;
+  cudaGetDevice(&k.device);
+  k.sm_count = h->sm_count;
+  const simlod_config& c = h->cfg;
+  k.words = {(uint64_t)(uint32_t)c.root_min[0], (uint64_t)(uint32_t)c.root_min[1],
+             (uint64_t)(uint32_t)c.root_min[2], c.root_log2, c.leaf_capacity, c.chunk_points,
+             c.grid_log2, c.max_expand_iters, c.max_batch_points, c.spill_capacity,
+             c.backlog_capacity, c.max_nodes, h->lay.data_bytes};
+  k.words.insert(k.words.end(), counts, counts + n);
+  return k;
+}
+
+}  // namespace
+
 SIMLOD_API int simlod_plan_autotune(simlod_t* h, const simlod_point* const* d_batches,
                                     const uint64_t* counts, uint32_t n_batches, void* stream,
                                     simlod_plan_params* best, double* best_ms) {
   if (!h || !best || (n_batches && (!d_batches || !counts))) return SIMLOD_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const TuneKey key = tune_key(h, counts, n_batches);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      *best = it->second.p;
+      if (best_ms) *best_ms = it->second.ms;
+      return simlod_reset(h, s);
+    }
+  }
   const uint64_t mb = h->cfg.max_batch_points;
-  std::vector<uint64_t> merges = {0};
-  for (uint64_t m : {1ull << 18, 1ull << 20, 1ull << 21, 1ull << 22, 1ull << 23})
-    if (m < mb) merges.push_back(m);
-  merges.push_back(mb);
-  const unsigned per_sm = (unsigned)h->fused_max_per_sm;
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
     return SIMLOD_ERR_CUDA;
   double best_t = -1.0;
-  for (unsigned bps = 1; bps <= std::max(1u, std::min(per_sm, 2u)); ++bps) {
-    for (uint64_t m : merges) {
-      simlod_plan_params p{m, bps, 1, 0};
-      simlod_plan_t* P = nullptr;
-      if (simlod_reset(h, s) != SIMLOD_OK) continue;
-      if (simlod_plan_create(h, d_batches, counts, n_batches, &p, &P) != SIMLOD_OK) continue;
-      auto ran = [&] {  // rejected batches are fine; device errors are not
-        const int r = simlod_sync(h);
-        return r == SIMLOD_OK || r == SIMLOD_ERR_OUT_OF_BOUNDS;
-      };
-      float ms = -1.0f;
-      if (simlod_plan_run(P, s) == SIMLOD_OK && ran() && simlod_reset(h, s) == SIMLOD_OK &&
-          cudaEventRecord(a, s) == cudaSuccess && simlod_plan_run(P, s) == SIMLOD_OK &&
-          cudaEventRecord(b, s) == cudaSuccess && ran())
-        cudaEventElapsedTime(&ms, a, b);
-      simlod_plan_destroy(P);
-      if (ms >= 0.0f && (best_t < 0.0 || ms < best_t)) {
-        best_t = ms;
-        *best = p;
-      }
+  auto trial = [&](const simlod_plan_params& p) {
+    simlod_plan_t* P = nullptr;
+    if (simlod_reset(h, s) != SIMLOD_OK) return;
+    if (simlod_plan_create(h, d_batches, counts, n_batches, &p, &P) != SIMLOD_OK) return;
+    auto ran = [&] {  // rejected batches are fine; device errors are not
+      const int r = simlod_sync(h);
+      return r == SIMLOD_OK || r == SIMLOD_ERR_OUT_OF_BOUNDS;
+    };
+    float ms = -1.0f;
+    if (simlod_plan_run(P, s) == SIMLOD_OK && ran() && simlod_reset(h, s) == SIMLOD_OK &&
+        cudaEventRecord(a, s) == cudaSuccess && simlod_plan_run(P, s) == SIMLOD_OK &&
+        cudaEventRecord(b, s) == cudaSuccess && ran())
+      cudaEventElapsedTime(&ms, a, b);
+    simlod_plan_destroy(P);
+    if (ms >= 0.0f && (best_t < 0.0 || ms < best_t)) {
+      best_t = ms;
+      *best = p;
     }
+  };
+  // stage 1: every kernel instance at its largest and half its largest
+  // width, updates merged up to the largest batch the octree takes
+  for (uint32_t v = 0; v < SL_N_VARIANTS; ++v) {
+    const int mx = h->var[v].max_per_sm;
+    if (mx < 1) continue;
+    trial(simlod_plan_params{mb, (uint32_t)mx, 1, v});
+    if (mx >= 2) trial(simlod_plan_params{mb, (uint32_t)(mx / 2), 1, v});
+  }
+  // stage 2: every merge size for the fastest instance and width
+  if (best_t >= 0.0) {
+    const simlod_plan_params top = *best;
+    for (uint64_t m : {0ull, 1ull << 18, 1ull << 20, 1ull << 21, 1ull << 22, 1ull << 23})
+      if (m < mb) trial(simlod_plan_params{m, top.blocks_per_sm, 1, top.variant});
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   const int rr = simlod_reset(h, s);
   if (best_t < 0.0) return SIMLOD_ERR_CUDA;
   if (best_ms) *best_ms = best_t;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = TuneChoice{*best, best_t};
+  }
   return rr;
+}
+
+SIMLOD_API int simlod_variant_info(uint32_t variant, simlod_variant_desc* out) {
+  if (!out || variant >= SL_N_VARIANTS) return SIMLOD_ERR_INVALID_ARG;
+  sl_variant_info v;
+  const int rc = kVariants[variant].info(&v);
+  cudaGetLastError();
+  out->threads_per_block = v.block;
+  out->max_blocks_per_sm = rc == 0 && v.max_per_sm > 0 ? (uint32_t)v.max_per_sm : 0u;
+  out->node_cache = v.node_cache;
+  out->store_unroll = v.store_unroll;
+  out->descent_group = v.descent_group;
+  out->smem_bytes = v.smem_bytes;
+  return out->max_blocks_per_sm ? SIMLOD_OK : SIMLOD_ERR_CUDA;
 }
 
 SIMLOD_API int simlod_set_launch_width(simlod_t* h, uint32_t blocks_per_sm,
@@ -971,6 +1118,13 @@ SIMLOD_API int simlod_set_launch_width(simlod_t* h, uint32_t blocks_per_sm,
   if (blocks_per_sm > (uint32_t)h->fused_max_per_sm) return SIMLOD_ERR_INVALID_ARG;
   const int bps = blocks_per_sm ? (int)blocks_per_sm : h->fused_max_per_sm;
   h->fused_grid = bps * h->sm_count;
+  return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_set_wait_limits(simlod_t* h, uint64_t barrier_ns, uint64_t ready_ns) {
+  if (!h) return SIMLOD_ERR_INVALID_ARG;
+  h->ctx.bar_ns = barrier_ns ? barrier_ns : FUSED_BARRIER_NS;
+  h->ctx.ready_ns = ready_ns ? ready_ns : FUSED_READY_NS;
   return SIMLOD_OK;
 }
 

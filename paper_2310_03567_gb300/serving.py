@@ -3,11 +3,14 @@ an HBM budget, continuous batching of each octree's queued requests into one
 persistent launch, and a per-frame render of every octree (Section 6) between
 the updates (Section 7.2's interleaving of updates and frames).
 
-Every octree has its own CUDA stream and arena. A request (points of one
-octree, in pinned host memory) is admitted when its device copy fits the HBM
-budget left by the arenas and the requests in flight; it is copied on the
-server's copy stream, so that the copy overlaps the launches running on its
-octree's stream, and the launch that applies it waits for the copy's event.
+Every octree has its own CUDA stream and arena. The HBM budget left by the
+arenas becomes one device staging buffer, allocated once when the server
+starts, so that nothing allocates device memory while requests are served. A
+request (points of one octree, in pinned host memory) is admitted, in arrival
+order, when its device copy fits a free range of that buffer; it is copied on
+the server's copy stream, so that the copy overlaps the launches running on
+its octree's stream, and the launch that applies it waits for the copy's
+event. Its range is freed when the launch that read it has finished.
 When a launch slot is free, the octree with the oldest
 admitted request gets one fused launch (simlod_insert_batches) over its
 admitted requests, each request one batch, in arrival order, up to
@@ -30,6 +33,7 @@ after another (the tests compare both byte for byte).
 from __future__ import annotations
 
 import dataclasses
+import gc
 import time
 
 import numpy as np
@@ -46,9 +50,11 @@ class Request:
     arrival: float  # seconds on the server clock
     rid: int = 0
     admitted: float = -1.0
+    launched: float = -1.0
     done: float = -1.0
-    dev: object = None  # device copy while in flight
+    dev: object = None  # device copy while in flight (a view of the staging buffer)
     ready: object = None  # event: the device copy is complete
+    slot: int = -1  # byte offset of the device copy in the staging buffer
 
     @property
     def n(self) -> int:
@@ -66,12 +72,52 @@ class OctreeSpec:
     camera: object = None  # 16 float32 view-projection for its frames
 
 
+class StagingPool:
+    """First-fit ranges of one device buffer of `size` bytes (offsets are
+    multiples of `align`); freed ranges merge with their free neighbours."""
+
+    def __init__(self, size: int, align: int = 256):
+        self.align = align
+        self.size = size // align * align
+        self.free = [(0, self.size)] if self.size else []  # (offset, bytes), sorted
+
+    def alloc(self, nbytes: int) -> int:
+        """Offset of a free range of nbytes, or -1 when none is large enough."""
+        need = max(self.align, -(-nbytes // self.align) * self.align)
+        for i, (o, n) in enumerate(self.free):
+            if n >= need:
+                if n == need:
+                    del self.free[i]
+                else:
+                    self.free[i] = (o + need, n - need)
+                return o
+        return -1
+
+    def release(self, offset: int, nbytes: int) -> None:
+        need = max(self.align, -(-nbytes // self.align) * self.align)
+        i = 0
+        while i < len(self.free) and self.free[i][0] < offset:
+            i += 1
+        self.free.insert(i, (offset, need))
+        if i + 1 < len(self.free) and offset + need == self.free[i + 1][0]:
+            self.free[i] = (offset, need + self.free[i + 1][1])
+            del self.free[i + 1]
+        if i > 0 and self.free[i - 1][0] + self.free[i - 1][1] == offset:
+            self.free[i - 1] = (self.free[i - 1][0], self.free[i - 1][1] + self.free[i][1])
+            del self.free[i]
+
+    def free_bytes(self) -> int:
+        return sum(n for _, n in self.free)
+
+
 class Server:
     def __init__(self, specs, hbm_budget: int, compute_slots: int = 2, frame_ms: float = 0.0,
                  max_batches_per_launch: int = 64, max_points_per_launch: int = 8_000_000,
-                 plain: bool = False):
+                 plain: bool = False, staging_cap: int = 8 << 30):
         """plain=True serves with the plain per-kernel path instead: one
-        request per update, one update at a time (the baseline)."""
+        request per update, one update at a time (the baseline). The budget
+        left by the arenas, at most staging_cap bytes, is the staging buffer
+        of the requests in flight."""
         import torch
         self.torch = torch
         if compute_slots < 1:
@@ -102,6 +148,9 @@ class Server:
             self.frames.append(None)
         if self.used > self.budget:
             raise ValueError("the arenas alone exceed the HBM budget")
+        self.pool = StagingPool(min(self.budget - self.used, int(staging_cap)))
+        self.stage = torch.empty(max(self.pool.size, 1), dtype=torch.uint8, device="cuda")
+        self.used += self.pool.size
         self.copy_stream = torch.cuda.Stream()
         self.pending = []      # arrived, not admitted (arrival order)
         self.queued = [[] for _ in self.trees]   # admitted, not launched, per octree
@@ -110,6 +159,21 @@ class Server:
         self.finished = []
         self.frame_times = []
         self.frame_waits = []
+        self.launches = 0
+        self.t0 = None
+
+    def reset(self):
+        """Empty every octree and the server's queues (nothing may be in
+        flight), keeping the arenas and the staging buffer."""
+        if self.inflight or self.pending or any(self.queued):
+            raise RuntimeError("reset with requests in flight")
+        for tree in self.trees:
+            tree.reset()
+            if tree.sync() != simlod.OK:
+                raise simlod.SimlodError(tree.sync(), "reset")
+        self.pool = StagingPool(self.pool.size)
+        self.finished, self.frame_times, self.frame_waits = [], [], []
+        self.busy = [False] * len(self.trees)
         self.launches = 0
         self.t0 = None
 
@@ -126,7 +190,8 @@ class Server:
                 for r in reqs:
                     r.done = t
                     r.dev = r.ready = None
-                    self.used -= r.nbytes
+                    self.pool.release(r.slot, r.nbytes)
+                    r.slot = -1
                     self.finished.append(r)
                 self.busy[k] = False
             else:
@@ -135,14 +200,18 @@ class Server:
 
     def _admit(self):
         torch = self.torch
-        while self.pending and self.used + self.pending[0].nbytes <= self.budget:
-            r = self.pending.pop(0)
+        while self.pending:
+            r = self.pending[0]
+            off = self.pool.alloc(r.nbytes)
+            if off < 0:
+                return  # arrival order: later requests wait behind this one
+            self.pending.pop(0)
+            r.slot = off
+            r.dev = self.stage[off:off + r.nbytes].view(r.n, 16)
             with torch.cuda.stream(self.copy_stream):
-                r.dev = torch.empty_like(r.points, device="cuda")
                 r.dev.copy_(r.points, non_blocking=True)
                 r.ready = torch.cuda.Event()
                 r.ready.record(self.copy_stream)
-            self.used += r.nbytes
             r.admitted = self.now()
             self.queued[r.octree].append(r)
 
@@ -157,9 +226,10 @@ class Server:
             take = launch_take([r.n for r in q], self.max_batches, self.max_points)
             reqs, self.queued[k] = q[:take], q[take:]
             tree = self.trees[k]
+            t = self.now()
             for r in reqs:
                 tree.stream.wait_event(r.ready)
-                r.dev.record_stream(tree.stream)
+                r.launched = t
             if self.plain:
                 rc = tree.insert(reqs[0].dev, stream=tree.stream, check=False)
             else:
@@ -195,11 +265,20 @@ class Server:
         """Serve `requests` (sorted by arrival) in real time; returns the
         finished requests."""
         reqs = sorted(requests, key=lambda r: r.arrival)
-        room = self.budget - sum(t.arena.numel() for t in self.trees)
         for i, r in enumerate(reqs):
             r.rid = i
-            if r.nbytes > room:
+            if r.nbytes > self.pool.size:
                 raise ValueError(f"request {i} ({r.nbytes} bytes) can never fit the HBM budget")
+        # no collector pauses inside the served latencies
+        gc_was = gc.isenabled()
+        gc.disable()
+        try:
+            return self._serve(reqs, idle_sleep)
+        finally:
+            if gc_was:
+                gc.enable()
+
+    def _serve(self, reqs, idle_sleep: float):
         self.t0 = time.perf_counter()
         nxt = 0
         next_frame = self.frame_ms / 1e3 if self.frame_ms else None
@@ -242,12 +321,18 @@ class Server:
         span = max(r.done for r in self.finished) - min(r.arrival for r in self.finished)
         ft = np.array(self.frame_times) * 1e3 if self.frame_times else np.zeros(1)
         fw = np.array(self.frame_waits) * 1e3 if self.frame_waits else np.zeros(1)
+        queue = np.array([r.launched - r.admitted for r in self.finished]) * 1e3
+        service = np.array([r.done - r.launched for r in self.finished]) * 1e3
         return {"requests": len(self.finished), "points": pts, "seconds": span,
                 "mpts_per_s": pts / span / 1e6 if span > 0 else 0.0,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)),
                                "p99": float(np.percentile(lat, 99))},
                 "admission_wait_ms": {"p50": float(np.percentile(wait, 50)),
                                       "p99": float(np.percentile(wait, 99))},
+                "launch_wait_ms": {"p50": float(np.percentile(queue, 50)),
+                                   "p99": float(np.percentile(queue, 99))},
+                "service_ms": {"p50": float(np.percentile(service, 50)),
+                               "p99": float(np.percentile(service, 99))},
                 "launches": self.launches, "frames": len(self.frame_times),
                 "frame_ms": {"p50": float(np.percentile(ft, 50)),
                              "p99": float(np.percentile(ft, 99))},
@@ -257,6 +342,7 @@ class Server:
     def close(self):
         for t in self.trees:
             t.close()
+        self.stage = None
 
 
 def launch_take(sizes, max_batches: int, max_points: int) -> int:

@@ -121,22 +121,46 @@ SIGNATURES = {
                                           _P, _U64, _P, _P]),
     "simlod_render": (_I32, [_P, _P, _U32, _U32, _P, _I32, _P]),
     "simlod_set_launch_width": (_I32, [_P, _U32, ctypes.POINTER(_U32)]),
+    "simlod_set_wait_limits": (_I32, [_P, _U64, _U64]),
     "simlod_restore": (_I32, [_P, ctypes.POINTER(Snapshot_t), _P]),
     "simlod_plan_create": (_I32, [_P, _P, _P, _U32, _P, ctypes.POINTER(_P)]),
     "simlod_plan_run": (_I32, [_P, _P]),
     "simlod_plan_info": (_I32, [_P, _P, ctypes.POINTER(_U32)]),
     "simlod_plan_destroy": (_I32, [_P]),
     "simlod_plan_autotune": (_I32, [_P, _P, _P, _U32, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "simlod_variant_info": (_I32, [_U32, _P]),
 }
 
 
 class PlanParams(ctypes.Structure):
     _fields_ = [("merge_points", ctypes.c_uint64), ("blocks_per_sm", ctypes.c_uint32),
-                ("use_graph", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("use_graph", ctypes.c_uint32), ("variant", ctypes.c_uint32)]
 
     def as_dict(self):
         return {"merge_points": int(self.merge_points), "blocks_per_sm": int(self.blocks_per_sm),
-                "use_graph": int(self.use_graph)}
+                "use_graph": int(self.use_graph), "variant": int(self.variant)}
+
+
+class VariantDesc(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in (
+        "threads_per_block", "max_blocks_per_sm", "node_cache", "store_unroll", "descent_group",
+        "smem_bytes")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+N_VARIANTS = 4  # SIMLOD_N_VARIANTS
+
+
+def variant_info(variant: int) -> dict:
+    """Block and tile parameters of kernel instance `variant` on the current
+    device (simlod_variant_info)."""
+    d = VariantDesc()
+    rc = load().simlod_variant_info(variant, ctypes.byref(d))
+    if rc != OK:
+        raise SimlodError(rc, "simlod_variant_info")
+    return d.as_dict()
 
 
 def load(path: str | None = None):
@@ -446,11 +470,19 @@ class Octree:
             raise SimlodError(rc, "simlod_set_launch_width")
         return int(mx.value)
 
+    def set_wait_limits(self, barrier_ns: int = 0, ready_ns: int = 0) -> None:
+        """Time limits of a persistent launch's grid-barrier and ready-flag
+        waits (0 = the default of 2 s)."""
+        rc = self._lib.simlod_set_wait_limits(self._h, barrier_ns, ready_ns)
+        if rc != OK:
+            raise SimlodError(rc, "simlod_set_wait_limits")
+
     def plan(self, ptrs, counts, merge_points: int = 0, blocks_per_sm: int = 0,
-             use_graph: bool = True) -> "Plan":
+             use_graph: bool = True, variant: int = 0) -> "Plan":
         """Batched form over raw 16-byte-aligned device pointers (kept by the
         plan; the caller keeps the buffers alive and orders their writes)."""
-        return Plan(self, ptrs, counts, PlanParams(merge_points, blocks_per_sm, int(use_graph), 0))
+        return Plan(self, ptrs, counts,
+                    PlanParams(merge_points, blocks_per_sm, int(use_graph), variant))
 
     def autotune(self, ptrs, counts, stream=None):
         """Fastest batched-form parameters for this batch list (resets the

@@ -37,9 +37,13 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_library_is_sm103a_only():
-    cmd = _build.library_command()
-    assert "arch=compute_103a,code=sm_103a" in cmd
-    assert sum(1 for a in cmd if a == "-gencode") == 1
+    cmds = [c for c, _ in _build.compile_commands()] + [_build.link_command(["x.o"], "x.so")]
+    for cmd in cmds:
+        assert "arch=compute_103a,code=sm_103a" in cmd
+        assert sum(1 for a in cmd if a == "-gencode") == 1
+    # every kernel instance of the autotuner is built, each in its own namespace
+    assert len(cmds) == len(_build.library_sources()) + len(_build.VARIANTS) + 1
+    assert len({a for c in cmds for a in c if a.startswith("-DSL_NS=")}) == len(_build.VARIANTS)
 
 
 def test_no_oracle_on_the_product_path():
@@ -134,3 +138,14 @@ def test_status_strings(lib):
         s = simlod.status_string(code)
         assert s and s != "unknown status"
     assert simlod.status_string(-99) == "unknown status"
+
+
+def test_kernel_instance_count_agrees(lib):
+    text = open(HEADER).read()
+    n = int(re.search(r"#define SIMLOD_N_VARIANTS (\d+)", text).group(1))
+    internal = open(os.path.join(_build.CSRC_DIR, "variant.h")).read()
+    assert int(re.search(r"#define SL_N_VARIANTS (\d+)", internal).group(1)) == n
+    assert simlod.N_VARIANTS == n == len(_build.VARIANTS) + 1
+    d = simlod.VariantDesc()
+    assert lib.simlod_variant_info(n, ctypes.byref(d)) == simlod.ERR_INVALID_ARG
+    assert lib.simlod_variant_info(0, None) == simlod.ERR_INVALID_ARG

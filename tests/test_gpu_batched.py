@@ -90,15 +90,44 @@ def test_autotune_picks_parameters_that_build_the_same_octree():
     tree = make_tree(w)
     dev, ptrs, counts = device_batches(w)
     best, ms = tree.autotune(ptrs, counts)
-    assert ms > 0 and best.blocks_per_sm in (1, 2) and best.use_graph == 1
+    assert 0 <= best.variant < simlod.N_VARIANTS
+    mx = simlod.variant_info(best.variant)["max_blocks_per_sm"]
+    assert ms > 0 and 1 <= best.blocks_per_sm <= mx and best.use_graph == 1
     assert tree.stats()["points"] == 0  # the tuner leaves the octree empty
     plan = tree.plan(ptrs, counts, merge_points=best.merge_points,
-                     blocks_per_sm=best.blocks_per_sm)
+                     blocks_per_sm=best.blocks_per_sm, variant=best.variant)
+    assert plan.info()[0]["variant"] == best.variant
     assert plan.run() == simlod.OK and tree.sync() == simlod.OK
     want = oracle.static_build(oracle.Config.make(root_min=w.root_min, root_log2=w.root_log2),
                                w.stream())
     assert_snapshots_equal(tree.snapshot(), want)
     plan.close()
+    # the choice is kept for this device, configuration and batch list
+    again, ms2 = tree.autotune(ptrs, counts)
+    assert again.as_dict() == best.as_dict() and ms2 == ms
+    assert tree.stats()["points"] == 0
+
+
+@pytest.mark.parametrize("variant", range(simlod.N_VARIANTS))
+def test_every_kernel_instance_matches_the_oracle(variant):
+    """Every instance of the persistent kernel the autotuner chooses among
+    (other threads per block, blocks per SM, node-cache size, store unroll,
+    descent group) builds the oracle's octree, one update per batch and with
+    merged updates, at its full and its smallest width."""
+    desc = simlod.variant_info(variant)
+    assert desc["max_blocks_per_sm"] >= 1 and desc["threads_per_block"] in (256, 512, 1024)
+    w = mixed_stream(n=1_500_000, seed=13 + variant)
+    tree = make_tree(w)
+    dev, ptrs, counts = device_batches(w)
+    want = oracle.static_build(oracle.Config.make(root_min=w.root_min, root_log2=w.root_log2),
+                               w.stream())
+    for merge, bps in ((0, 0), (1 << 20, 1)):
+        plan = tree.plan(ptrs, counts, merge_points=merge, blocks_per_sm=bps, variant=variant)
+        tree.reset()
+        assert plan.run() == simlod.OK
+        assert tree.sync() == simlod.OK
+        assert_snapshots_equal(tree.snapshot(), want)
+        plan.close()
 
 
 def test_plan_rejects_bad_arguments():
@@ -110,4 +139,6 @@ def test_plan_rejects_bad_arguments():
     with pytest.raises(simlod.SimlodError):
         tree.plan(ptrs[:1], [(1 << 20) + 1])  # larger than max_batch_points
     with pytest.raises(simlod.SimlodError):
-        tree.plan(ptrs, counts, blocks_per_sm=3)
+        tree.plan(ptrs, counts, blocks_per_sm=simlod.variant_info(0)["max_blocks_per_sm"] + 1)
+    with pytest.raises(simlod.SimlodError):
+        tree.plan(ptrs, counts, variant=simlod.N_VARIANTS)

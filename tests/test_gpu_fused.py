@@ -322,3 +322,33 @@ def test_most_batches_per_launch_and_one_more():
     st = t.stats()
     assert st["points"] == len(pts) and st["batches"] == int((sizes > 0).sum())
     assert_snapshots_equal(t.snapshot(), oracle.static_build(ocfg(**kw), pts))
+
+
+def test_grid_barrier_times_out_with_every_block_present():
+    """A grid-barrier limit of 1 ns on an ordinary launch (every block is
+    resident and arrives, so nothing can hang): the first block that has to
+    wait gives up after its first few polls, the launch ends with a TIMEOUT
+    status, the handle is poisoned, and a reset handle with the default limit
+    builds the oracle's octree again."""
+    w = synth.aerial_workload(n=4_000_000)
+    dev = simlod.points_tensor(w.points)
+    ptrs = [dev.data_ptr() + int(o) * 16 for o in w.offsets]
+    counts = [int(c) for c in w.counts]
+    t = make_tree(1 << 30, root_log2=22)
+    t.set_wait_limits(barrier_ns=1)
+    rc = simlod.OK
+    for _ in range(5):  # a launch whose every barrier completes in a few polls would pass
+        t.reset()
+        assert t.insert_many_ptrs(ptrs, counts) == simlod.OK
+        rc = t.sync()
+        if rc != simlod.OK:
+            break
+    assert rc == simlod.ERR_TIMEOUT
+    assert t.stats()["sticky_status"] == simlod.ERR_TIMEOUT
+    assert t.insert(simlod.points_tensor(w.points[:10]), check=False) == simlod.ERR_POISONED
+    t.set_wait_limits()  # back to the default limits
+    t.reset()
+    assert t.insert_many_ptrs(ptrs, counts) == simlod.OK
+    assert t.sync() == simlod.OK
+    assert_snapshots_equal(t.snapshot(),
+                           oracle.static_build(oracle.Config.make(root_log2=22), w.points))

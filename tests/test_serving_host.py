@@ -42,3 +42,42 @@ def test_launch_take_caps():
     assert take([150, 10], 64, 100) == 1          # one oversized request still goes
     assert take([60, 50, 1], 64, 100) == 1        # stops at the first that overflows
     assert take([], 64, 100) == 0
+
+
+def test_staging_pool_first_fit_and_merge():
+    pool = serving.StagingPool(4096, align=256)
+    a = pool.alloc(1000)        # 1024 bytes
+    b = pool.alloc(256)
+    c = pool.alloc(2000)        # 2048 bytes
+    assert (a, b, c) == (0, 1024, 1280)
+    assert pool.alloc(1024) == -1 and pool.free_bytes() == 768
+    pool.release(b, 256)
+    assert pool.alloc(300) == 3328          # first fit: the hole at 1024 is too small
+    pool.release(a, 1000)
+    assert pool.free == [(0, 1280), (3840, 256)]  # a merged with the hole b left
+    pool.release(c, 2000)
+    pool.release(3328, 300)
+    assert pool.free == [(0, 4096)] and pool.free_bytes() == 4096
+
+
+def test_staging_pool_random_use_never_overlaps():
+    rng = np.random.default_rng(7)
+    pool = serving.StagingPool(1 << 20, align=256)
+    live = {}
+    for _ in range(2000):
+        if live and rng.random() < 0.45:
+            off = list(live)[int(rng.integers(len(live)))]
+            pool.release(off, live.pop(off))
+        else:
+            n = int(rng.integers(1, 60_000))
+            off = pool.alloc(n)
+            if off >= 0:
+                assert off % 256 == 0 and off + n <= pool.size
+                for o, m in live.items():
+                    assert off + n <= o or o + m <= off
+                live[off] = n
+        used = sum(-(-m // 256) * 256 for m in live.values())
+        assert used + pool.free_bytes() == pool.size
+    for off, n in list(live.items()):
+        pool.release(off, n)
+    assert pool.free == [(0, pool.size)]

@@ -1,13 +1,15 @@
-"""The no-allocation entry point gives the same voxels as the arena path.
+"""The no-allocation entry point gives the oracle's voxels and allocates nothing.
 
 simlod_sample_node_noalloc is meant for callers that cannot allocate device
 memory when they need voxel sampling (a running frame loop, or code that lives
 inside another framework's memory management): its scratch is a fixed device
 array in the library instead of a caller arena. Here it is called through the
-C ABI twice in a row, with different batches, and each result must equal the
-root voxels that the regular insert path (simlod_insert_batch into a fresh
-octree whose root splits) produces for the same points. Voxels are integers,
-so the comparison is exact.
+C ABI twice in a row, with different batches. Each result must equal the root
+voxels of the oracle's closed-form octree of the same points (oracle/static.c)
+and those of the regular insert path (simlod_insert_batch into a fresh octree
+whose root splits). Voxels are integers, so the comparisons are exact. A
+further call must leave the device's free memory and torch's allocated bytes
+unchanged.
 
 This file sorts last on purpose, so that a run stopping at the first failure
 has already run every other test.
@@ -17,6 +19,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_2310_03567_gb300 import simlod, synth
 
 pytestmark = pytest.mark.gpu
@@ -59,23 +62,65 @@ def _root_voxels_by_insert(pts: np.ndarray) -> np.ndarray:
     return out
 
 
-def test_noalloc_matches_insert_path_twice():
+def _root_voxels_by_oracle(pts: np.ndarray) -> np.ndarray:
+    cfg = oracle.Config.make(root_log2=L, leaf_capacity=1000, grid_log2=G)
+    snap = oracle.static_build(cfg, pts)
+    root = snap.nodes[0]
+    assert root["level"] == 0 and root["is_inner"] == 1
+    out = snap.voxels[:int(root["n_voxels"])]  # the root's voxels come first
+    # the oracle's voxel records have the same fields and layout
+    assert out.dtype.names == simlod.VOXEL_REC_DTYPE.names
+    return out.view(simlod.VOXEL_REC_DTYPE)
+
+
+def test_noalloc_matches_oracle_and_insert_path_twice():
     stream = torch.cuda.Stream()
     # call 1: points spread over the whole cube (mostly one point per cell)
     a = synth.uniform(101, 1 << L, 100_000)
-    # call 2: the largest accepted batch packed into 4^3 cells, so that many
-    # points from many warps contend for each cell and stale table entries
-    # from call 1 would show up
+    # call 2: the largest accepted batch packed into a 2^11 cube (about 5^3
+    # cells of 512 units), so that many points from many warps contend for
+    # each cell and stale table entries from call 1 would show up
     b = synth.uniform(102, 1 << 11, simlod_max())
     b["x"] += 20_000
     b["y"] += 3_000
     b["z"] += 41_000
     got_a = _noalloc(a, stream)
     got_b = _noalloc(b, stream)
-    want_a = _root_voxels_by_insert(a)
-    want_b = _root_voxels_by_insert(b)
-    assert len(got_a) == len(want_a) and np.array_equal(got_a, want_a)
-    assert len(got_b) == len(want_b) and np.array_equal(got_b, want_b)
+    for got, pts in ((got_a, a), (got_b, b)):
+        want = _root_voxels_by_oracle(pts)
+        assert len(got) == len(want) and np.array_equal(got, want)
+        by_insert = _root_voxels_by_insert(pts)
+        assert len(got) == len(by_insert) and np.array_equal(got, by_insert)
+
+
+def test_noalloc_allocates_nothing():
+    lib = simlod.load()
+    stream = torch.cuda.Stream()
+    pts = synth.uniform(103, 1 << L, 50_000)
+    d_pts = simlod.points_tensor(pts)
+    d_out = torch.empty((len(pts), simlod.VOXEL_REC_DTYPE.itemsize), dtype=torch.uint8,
+                        device="cuda")
+    d_cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream.wait_stream(torch.cuda.current_stream())
+
+    def call():
+        rc = lib.simlod_sample_node_noalloc(d_pts.data_ptr(), len(pts),
+                                            (ctypes.c_int32 * 3)(0, 0, 0), L, G,
+                                            d_out.data_ptr(), len(pts), d_cnt.data_ptr(),
+                                            stream.cuda_stream)
+        assert rc == simlod.OK, simlod.status_string(rc)
+        stream.synchronize()
+
+    call()  # warm-up: the first call in the context loads the device code
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    call()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 == free0
+    assert 0 < int(d_cnt.item()) <= len(pts)
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
