@@ -128,7 +128,7 @@ __device__ __forceinline__ void splat(const View& v, int4 r, unsigned long long*
   atomicMin(fb + (uint64_t)py * v.width + px, key);
 }
 
-// One warp per drawn node: walk its chunk list (Listing 2's loop, with the
+// One warp per drawn node: walk its chunk list (Section 6's chunk loop, with the
 // next link loaded before the chunk's records are drawn) and splat every
 // point (leaf) or voxel (inner node).
 __global__ void k_render_draw(Ctx c, View v, const uint32_t* vis, unsigned long long* fb) {

@@ -1459,7 +1459,7 @@ SIMLOD_API int simlod_snapshot(simlod_t* h, simlod_snapshot_t* snap) {
     r.log2size = h->cfg.root_log2 - m.level;
     r.n_points = inner ? 0 : num[i];
     r.n_voxels = inner ? num[i] : 0;
-    // walk the linked list, as a renderer would (Listing 1)
+    // walk the linked list, as a renderer would (Section 6)
     uint64_t walked = 0, idx = 0;
     for (uint32_t ref = m.head; ref != NONE && walked <= m.n_chunks; ++walked) {
       const uint64_t off = (uint64_t)ref * REF_BYTES;
