@@ -272,6 +272,19 @@ def rank_workload(name: str, points, rank: int, morton: bool = False):
     return w, root_log2
 
 
+def prefix_workload(w, k: int):
+    """The first k batches of workload w, as a workload of their own (the
+    points of those batches only, in insertion order)."""
+    from paper_2310_03567_gb300 import synth
+    k = max(1, min(k, len(w.counts)))
+    pts = np.concatenate([w.points[int(o):int(o) + int(c)]
+                          for o, c in zip(w.offsets[:k], w.counts[:k])])
+    cnt = w.counts[:k].copy()
+    off = np.concatenate([[0], np.cumsum(cnt)[:-1]]).astype(np.uint64)
+    return synth.Workload(f"{w.name}-first{k}", pts, off, cnt, w.root_min, w.root_log2,
+                          w.recipe + f"; its first {k} batches")
+
+
 def aggregate(ms_local: float, points_local: int, dist=None, device="cpu"):
     """Whole-job timing across ranks: the slowest rank's time and the total
     points of all ranks (value = total / max time)."""
@@ -312,6 +325,8 @@ def run_ours(args):
 
     # each rank builds its own octree from its own stream (independent units)
     w, root_log2 = rank_workload(args.workload, args.points, rank, args.morton)
+    if args.batches:  # a prefix of the stream (profiling of a small case)
+        w = prefix_workload(w, args.batches)
     n_points = w.n_points
     dev_pts = simlod.points_tensor(w.points)
     ptrs = [dev_pts.data_ptr() + int(o) * 16 for o in w.offsets]
@@ -418,7 +433,27 @@ def run_ours(args):
     render = {"ms": r0.elapsed_time(r1) / 5, "width": 1920, "height": 1080,
               "nodes": rst["render_nodes"], "samples": rst["render_samples"],
               "pixels_hit": int((frame != -1).sum().item())}
-    del frame
+    # ---- compaction of every node into a contiguous array (simlod_compact),
+    # and the same frame again
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    before = frame.clone()
+    c0.record(stream)
+    tree.compact(0)
+    c1.record(stream)
+    tree.render(cam, frame)
+    r0.record(stream)
+    for _ in range(5):
+        tree.render(cam, frame)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    check(tree.sync(), "compact")
+    cst = tree.stats()
+    render["compacted"] = {"compact_ms": c0.elapsed_time(c1), "nodes": cst["compact_nodes"],
+                           "chunks_freed": cst["compact_chunks_freed"],
+                           "render_ms": r0.elapsed_time(r1) / 5,
+                           "same_frame": bool(torch.equal(before, frame))}
+    del frame, before
 
     # ---- end to end through the public API: pinned host stream -> HBM,
     # fused update, result (stats) back to the host, every step
@@ -585,7 +620,7 @@ def run_ours(args):
     tree.close()
     del tree, dev_pts
     torch.cuda.empty_cache()
-    forms = args.forms and args.workload == "clustered" and not args.morton
+    forms = args.forms and args.workload == "clustered" and not args.morton and not args.batches
     if forms and world == 1:
         # the two forms built on the update, each on its own workload
         line["batched"] = batched_form(args)
@@ -957,6 +992,8 @@ def main():
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the batched and serving sub-measurements of the default run")
     ap.add_argument("--points", type=int, default=None)
+    ap.add_argument("--batches", type=int, default=None,
+                    help="only the first BATCHES batches of the workload (small profiling cases)")
     ap.add_argument("--ref-points", type=int, default=1_000_000,
                     help="reference arm: the first batches of the workload up to at least this "
                          "many points, per step")

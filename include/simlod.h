@@ -118,6 +118,11 @@ typedef struct {
   uint32_t device_error_bits;
   /* the last simlod_render: nodes drawn, points and voxels visited */
   uint64_t render_nodes, render_samples;
+  /* compaction (simlod_compact): nodes that are arrays now and the chunks
+   * they stand in for; nodes turned into arrays and chunks given back to the
+   * pool since create/reset; arrays turned back into chunk lists by inserts */
+  uint64_t compact_nodes, compact_chunks, compacted_total, compact_chunks_freed,
+      decompacted_total;
 } simlod_stats;
 
 /* Per-kernel device time, accumulated while timing is enabled, and the
@@ -336,6 +341,19 @@ SIMLOD_API int simlod_get_stats(simlod_t* h, simlod_stats* out);
  * follow in node order sorted by cell. n_chunks is the length of the node's
  * chunk list, ceil(count / C) (Section 5.3). */
 SIMLOD_API int simlod_snapshot(simlod_t* h, simlod_snapshot_t* snap);
+
+/* Compaction of cold nodes (Section 8's direction of turning nodes that are
+ * no longer modified into non-growable arrays): every node whose records
+ * (points of a leaf, voxels of an inner node) fill two or more chunks and
+ * that has received none in the last idle_updates updates gets them copied,
+ * in order, into one contiguous array in the data region, and its chunks go
+ * back to the pool. The octree does not change: snapshots (n_chunks still
+ * reports ceil(count / C)), frames and later inserts are the same; an insert
+ * that adds records to a compacted node first turns it back into a chunk list
+ * (the array's space is not reused). Nodes the data region has no room for
+ * stay as they are. Asynchronous on `stream`, ordered after the inserts
+ * before it; simlod_get_stats reports the counts. */
+SIMLOD_API int simlod_compact(simlod_t* h, uint32_t idle_updates, void* stream);
 
 /* Section 6: draw the octree into a caller-owned device framebuffer of
  * width * height uint64_t entries (row-major, 8-byte aligned), each

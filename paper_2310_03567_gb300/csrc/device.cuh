@@ -157,6 +157,12 @@ struct Ctl {
   unsigned int mv_count[2];              // entries of the two mover lists
   unsigned long long render_samples;     // points and voxels visited by the last render
   unsigned long long phase_ns[8];        // fused form: time per phase (see PH_*)
+  unsigned long long st_compacted;       // nodes turned into arrays (simlod_compact), in all
+  unsigned long long st_compact_chunks;  // chunks those nodes gave back to the pool
+  unsigned long long st_decompacted;     // arrays turned back into chunk lists by an insert
+  unsigned long long compact_now;        // nodes that are arrays now
+  unsigned long long compact_chunks_now; // chunks those arrays stand in for
+  unsigned long long pad_ctl;
 };
 static_assert(sizeof(Ctl) % 16 == 0, "Ctl size");
 
@@ -174,7 +180,9 @@ struct NodeMeta {
   uint32_t st_tail;     //   the tail before allocation,
   uint32_t st_seq;      //   first alloc_refs entry of the newly allocated chunks,
   uint32_t st_base;     //   and the records stored before this update
-  uint32_t pad[4];
+  uint32_t touched;     // updates applied when the node last received records (1 = the first)
+  uint32_t compact;     // 1: the records are one contiguous array (head), not a chunk list
+  uint32_t pad[2];
 };
 static_assert(sizeof(NodeMeta) == 64, "NodeMeta size");
 static_assert(offsetof(NodeMeta, st_nch) == 32 && offsetof(NodeMeta, st_base) == 44,
@@ -273,9 +281,29 @@ __device__ __forceinline__ uint32_t* chunk_aux(const Ctx& c, uint32_t ref) {
   return reinterpret_cast<uint32_t*>(ref_ptr(c, ref) + CHUNK_HEADER + 16u * c.C);
 }
 
+// A compacted node's records: one array in the data region, a chunk header
+// (next = NONE, then the capacity) followed by cap records and cap aux words,
+// the layout of a chunk of cap records.
+__device__ __forceinline__ int4* array_recs(const Ctx& c, uint32_t ref) {
+  return reinterpret_cast<int4*>(ref_ptr(c, ref) + CHUNK_HEADER);
+}
+
+__device__ __forceinline__ uint32_t* array_aux(const Ctx& c, uint32_t ref, uint32_t cap) {
+  return reinterpret_cast<uint32_t*>(ref_ptr(c, ref) + CHUNK_HEADER + 16ull * cap);
+}
+
+__device__ __forceinline__ unsigned long long array_bytes(uint32_t cap) {
+  return ((CHUNK_HEADER + 20ull * cap) + REF_BYTES - 1) / REF_BYTES * REF_BYTES;
+}
+
 // A reference that stays inside the data region for `bytes` bytes.
 __device__ __forceinline__ bool ref_ok(const Ctx& c, uint32_t ref, uint32_t bytes) {
   return ref != NONE && (unsigned long long)ref * REF_BYTES + bytes <= c.data_bytes;
+}
+
+// An array of cap records at ref stays inside the data region.
+__device__ __forceinline__ bool array_ok(const Ctx& c, uint32_t ref, uint32_t cap) {
+  return ref != NONE && (unsigned long long)ref * REF_BYTES + array_bytes(cap) <= c.data_bytes;
 }
 
 __device__ __forceinline__ uint32_t* grid_words(const Ctx& c, uint32_t ref) {
@@ -1044,6 +1072,7 @@ __device__ void alloc_chunks(const Ctx& c, uint32_t id, uint32_t total, bool lea
     m.st_tail = tail;
     m.st_seq = k ? seq : 0u;
     m.st_base = c.num[id];
+    m.touched = (uint32_t)c.ctl->st_batches + 1u;
     c.scur[id] = 0;
   }
   if (!k || !ok) return;
@@ -1121,7 +1150,9 @@ __device__ void split_leaf(const Ctx& c, uint32_t id) {
     cm.st_tail = NONE;
     cm.st_seq = 0;
     cm.st_base = 0;
-    for (int q = 0; q < 4; ++q) cm.pad[q] = 0;
+    cm.touched = 0;
+    cm.compact = 0;
+    cm.pad[0] = cm.pad[1] = 0;
     c.meta[c0 + k] = cm;
     c.child[c0 + k] = NONE;
     c.gridref[c0 + k] = NONE;
@@ -1148,10 +1179,52 @@ __device__ void split_leaf(const Ctx& c, uint32_t id) {
   }
 }
 
+// All 32 lanes of a warp call: a compacted node (simlod_compact) that receives
+// records again goes back to a chunk list first: ceil(n / C) chunks, pool
+// first then bump, linked and noted in the leaf's directory, with its n
+// records copied in. The array's space is not reused.
+__device__ void restore_chunks(const Ctx& c, uint32_t id, bool leaf) {
+  NodeMeta& m = c.meta[id];
+  const uint32_t n = c.num[id], arr = m.head;
+  if (!array_ok(c, arr, n)) {
+    if (lane_id() == 0) set_error(c, E_INTERNAL);
+    return;
+  }
+  __syncwarp();
+  if (lane_id() == 0) {
+    m.n_chunks = 0;
+    m.head = m.tail = NONE;
+  }
+  __syncwarp();
+  alloc_chunks(c, id, n, leaf);
+  __syncwarp();
+  const uint32_t seq = m.st_seq, nch = m.n_chunks;
+  if (nch != (n + c.C - 1) / c.C || (unsigned long long)seq + nch > c.max_chunks) {
+    if (lane_id() == 0) set_error(c, E_INTERNAL);  // the allocation failed (error already set)
+    return;
+  }
+  const int4* src = array_recs(c, arr);
+  const uint32_t* sax = array_aux(c, arr, n);
+  for (uint32_t i = lane_id(); i < n; i += 32u) {
+    const uint32_t ref = c.alloc_refs[seq + i / c.C], q = i % c.C;
+    chunk_recs(c, ref)[q] = src[i];
+    chunk_aux(c, ref)[q] = sax[i];
+  }
+  __syncwarp();
+  if (lane_id() == 0) {
+    m.compact = 0;
+    atomicAdd(&c.ctl->st_decompacted, 1ull);
+    atomicAdd(&c.ctl->compact_now, ~0ull);  // minus one
+    atomicAdd(&c.ctl->compact_chunks_now, 0ull - nch);
+  }
+  __syncwarp();
+}
+
 // All 32 lanes of a warp call for one candidate node.
 __device__ __forceinline__ void decide_node(const Ctx& c, uint32_t id) {
   const uint32_t k = c.cnt[id];
   if (k == 0) return;
+  if (c.meta[id].compact) restore_chunks(c, id, c.child[id] == NONE);
   const uint32_t num = c.num[id];
   if (c.child[id] == NONE) {
     const uint32_t total = num + k;

@@ -140,6 +140,16 @@ __global__ void k_render_draw(Ctx c, View v, const uint32_t* vis, unsigned long 
     const uint32_t id = vis[k];
     const uint32_t n = c.num[id];
     const NodeMeta& m = c.meta[id];
+    if (m.compact) {  // one contiguous array (simlod_compact)
+      if (array_ok(c, m.head, n)) {
+        const int4* recs = array_recs(c, m.head);
+        for (uint32_t q = lane; q < n; q += 32) splat(v, recs[q], fb);
+      } else if (lane == 0) {
+        set_error(c, E_INTERNAL);
+      }
+      if (lane == 0) atomicAdd(&c.ctl->render_samples, (unsigned long long)n);
+      continue;
+    }
     const uint32_t nch = m.n_chunks;
     uint32_t ref = m.head, done = 0;
     for (uint32_t j = 0; j < nch && done < n; ++j) {

@@ -102,6 +102,82 @@ __global__ void __launch_bounds__(BLOCK) k_store(Ctx c, const int4* pts, uint64_
               blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
 
+// Compaction of cold nodes (the paper's closing direction: nodes that are no
+// longer modified become non-growable arrays). One warp per node: a node with
+// records in two or more chunks that has received none in the last `idle`
+// updates gets one contiguous array (records, then aux words) from the data
+// region, its records are copied over in order, and its chunks go back to
+// the pool. Space the data region cannot give is skipped without an error.
+__global__ void k_compact(Ctx c, uint32_t idle) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const uint64_t nwarps = (uint64_t)gridDim.x * blockDim.x / 32;
+  const uint32_t n_nodes = min(vload(&c.ctl->n_nodes), c.max_nodes);
+  const unsigned long long now = vload(&c.ctl->st_batches);
+  for (uint64_t id = warp; id < n_nodes; id += nwarps) {
+    NodeMeta& m = c.meta[id];
+    const uint32_t n = c.num[id], nch = m.n_chunks;
+    if (m.compact || n == 0 || nch < 2 || (unsigned long long)m.touched + idle > now) continue;
+    const unsigned long long bytes = array_bytes(n);
+    unsigned long long off = ~0ull;
+    int p0 = 0;
+    if (lane == 0) {
+      unsigned long long b = vload(&c.ctl->bump);
+      while (b + bytes <= c.data_bytes) {
+        const unsigned long long seen = atomicCAS(&c.ctl->bump, b, b + bytes);
+        if (seen == b) {
+          off = b;
+          break;
+        }
+        b = seen;
+      }
+      if (off != ~0ull) {
+        p0 = atomicAdd(&c.ctl->pool_top, (int)nch);
+        if (p0 < 0 || (unsigned long long)p0 + nch > c.max_chunks) {
+          set_error(c, E_POOL);
+          off = ~0ull;
+        }
+      }
+    }
+    off = __shfl_sync(FULL_MASK, off, 0);
+    p0 = __shfl_sync(FULL_MASK, p0, 0);
+    if (off == ~0ull) continue;
+    const uint32_t arr = (uint32_t)(off / REF_BYTES);
+    int4* drec = array_recs(c, arr);
+    uint32_t* daux = array_aux(c, arr, n);
+    uint32_t ref = m.head, idx = 0;
+    for (uint32_t j = 0; j < nch && idx < n; ++j) {
+      if (!ref_ok(c, ref, c.chunk_bytes)) {
+        if (lane == 0) set_error(c, E_INTERNAL);
+        break;
+      }
+      const uint32_t nxt = *chunk_next(c, ref);
+      const uint32_t cnt = min(c.C, n - idx);
+      const int4* srec = chunk_recs(c, ref);
+      const uint32_t* saux = chunk_aux(c, ref);
+      for (uint32_t q = lane; q < cnt; q += 32) {
+        drec[idx + q] = srec[q];
+        daux[idx + q] = saux[q];
+      }
+      if (lane == 0) c.pool[p0 + (int)j] = ref;
+      idx += cnt;
+      ref = nxt;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      uint32_t* hdr = reinterpret_cast<uint32_t*>(ref_ptr(c, arr));
+      hdr[0] = NONE;  // no next chunk
+      hdr[1] = n;     // capacity
+      m.head = m.tail = arr;
+      m.compact = 1;
+      atomicAdd(&c.ctl->st_compacted, 1ull);
+      atomicAdd(&c.ctl->st_compact_chunks, (unsigned long long)nch);
+      atomicAdd(&c.ctl->compact_now, 1ull);
+      atomicAdd(&c.ctl->compact_chunks_now, (unsigned long long)nch);
+    }
+  }
+}
+
 __global__ void k_end(Ctx c, uint64_t n, uint32_t iters) { phase_end(c, n, iters); }
 
 __global__ void k_end_rejected(Ctx c) { phase_end_rejected(c); }
@@ -1363,7 +1439,22 @@ SIMLOD_API int simlod_get_stats(simlod_t* h, simlod_stats* out) {
   out->device_error_bits = t.error;
   out->render_nodes = t.vis_count;
   out->render_samples = t.render_samples;
+  out->compact_nodes = t.compact_now;
+  out->compact_chunks = t.compact_chunks_now;
+  out->compacted_total = t.st_compacted;
+  out->compact_chunks_freed = t.st_compact_chunks;
+  out->decompacted_total = t.st_decompacted;
   return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_compact(simlod_t* h, uint32_t idle_updates, void* stream) {
+  if (!h) return SIMLOD_ERR_INVALID_ARG;
+  if (h->sticky) return SIMLOD_ERR_POISONED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  h->last_stream = s;
+  const Ctx& c = h->ctx;
+  k_compact<<<(unsigned)h->sm_count * 4, BLOCK, 0, s>>>(c, idle_updates);
+  return cudaGetLastError() == cudaSuccess ? SIMLOD_OK : poison(h, SIMLOD_ERR_CUDA);
 }
 
 SIMLOD_API int simlod_render(simlod_t* h, const float view_proj[16], uint32_t width,
@@ -1459,9 +1550,30 @@ SIMLOD_API int simlod_snapshot(simlod_t* h, simlod_snapshot_t* snap) {
     r.log2size = h->cfg.root_log2 - m.level;
     r.n_points = inner ? 0 : num[i];
     r.n_voxels = inner ? num[i] : 0;
-    // walk the linked list, as a renderer would (Section 6)
     uint64_t walked = 0, idx = 0;
-    for (uint32_t ref = m.head; ref != NONE && walked <= m.n_chunks; ++walked) {
+    if (m.compact) {  // one contiguous array (simlod_compact)
+      const uint64_t off = (uint64_t)m.head * REF_BYTES;
+      const uint64_t cap = num[i];
+      if (m.head == NONE || off + CHUNK_HEADER + 20 * cap > data.size()) {
+        bad = 1;
+      } else {
+        const int4* recs = reinterpret_cast<const int4*>(data.data() + off + CHUNK_HEADER);
+        const uint32_t* aux =
+            reinterpret_cast<const uint32_t*>(data.data() + off + CHUNK_HEADER + 16 * cap);
+        for (; idx < cap; ++idx) {
+          const int4 v = recs[idx];
+          if (inner) {
+            snap->voxels[vo + idx] = simlod_voxel_rec{aux[idx], v.x, v.y, v.z, (uint32_t)v.w};
+          } else {
+            snap->points[po + idx] = simlod_point_rec{v.x, v.y, v.z, (uint32_t)v.w, aux[idx]};
+          }
+        }
+      }
+      walked = (num[i] + C - 1) / C;  // the chunks the node would take
+    }
+    // walk the linked list, as a renderer would (Section 6)
+    for (uint32_t ref = m.compact ? NONE : m.head; ref != NONE && walked <= m.n_chunks;
+         ++walked) {
       const uint64_t off = (uint64_t)ref * REF_BYTES;
       if (off + chunk_bytes > data.size()) {
         bad = 1;

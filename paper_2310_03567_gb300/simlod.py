@@ -71,7 +71,12 @@ class Stats(ctypes.Structure):
         "last_iterations")] + [("sticky_status", ctypes.c_int32),
                                ("device_error_bits", ctypes.c_uint32),
                                ("render_nodes", ctypes.c_uint64),
-                               ("render_samples", ctypes.c_uint64)]
+                               ("render_samples", ctypes.c_uint64),
+                               ("compact_nodes", ctypes.c_uint64),
+                               ("compact_chunks", ctypes.c_uint64),
+                               ("compacted_total", ctypes.c_uint64),
+                               ("compact_chunks_freed", ctypes.c_uint64),
+                               ("decompacted_total", ctypes.c_uint64)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -129,6 +134,7 @@ SIGNATURES = {
     "simlod_plan_destroy": (_I32, [_P]),
     "simlod_plan_autotune": (_I32, [_P, _P, _P, _U32, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "simlod_variant_info": (_I32, [_U32, _P]),
+    "simlod_compact": (_I32, [_P, _U32, _P]),
 }
 
 
@@ -469,6 +475,14 @@ class Octree:
         if rc != OK:
             raise SimlodError(rc, "simlod_set_launch_width")
         return int(mx.value)
+
+    def compact(self, idle_updates: int = 0, stream=None) -> None:
+        """Turn the chunk lists of nodes idle for idle_updates updates into
+        contiguous arrays (simlod_compact); asynchronous on the stream."""
+        st = stream if stream is not None else self.stream
+        rc = self._lib.simlod_compact(self._h, idle_updates, _stream_ptr(st))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_compact")
 
     def set_wait_limits(self, barrier_ns: int = 0, ready_ns: int = 0) -> None:
         """Time limits of a persistent launch's grid-barrier and ready-flag

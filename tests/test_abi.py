@@ -128,6 +128,8 @@ def test_null_handles_are_rejected_before_cuda(lib):
         "simlod_restore": (None, None, None),
         "simlod_set_timing": (None, 1, 0),
         "simlod_get_timing": (None, None),
+        "simlod_set_wait_limits": (None, 0, 0),
+        "simlod_compact": (None, 0, None),
     }
     for name, args in calls.items():
         assert getattr(lib, name)(*args) == simlod.ERR_INVALID_ARG, name
