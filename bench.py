@@ -50,15 +50,15 @@ def update_alg_bytes(B, S, V, K, grid_bytes):
     return 16 * B + 20 * B + 40 * S + 16 * V + grid_bytes * K
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per inserted
-# point of one k_fused launch, from an ncu capture of the aerial scan's first
-# 10M points in 1M batches (the full 50M launch is too large to capture with
-# the full section set; traffic grows with the points processed). Keyed by a
-# hash of the kernel's sources: a changed kernel reports null until it has
-# been captured again.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_fused
+# launch over a whole workload (every batch of the stream: the launch the
+# bench times), from an ncu capture of that launch with the DRAM byte
+# counters alone (one pass, so nothing is replayed). Keyed by a hash of the
+# kernel's sources and by the workload: a changed kernel reports null until
+# it has been captured again.
 KERNEL_SOURCES = ("paper_2310_03567_gb300/csrc/device.cuh", "paper_2310_03567_gb300/csrc/fused.cuh",
                   "include/simlod.h", "paper_2310_03567_gb300/_build.py")
-TRAFFIC_PER_POINT = {"3be6fcb9a45f81a4": 190.40}
+TRAFFIC_PER_LAUNCH = {}
 
 
 def kernel_source_hash():
@@ -574,8 +574,7 @@ def run_ours(args):
         fused_unmerged = {"value": value, "ms_per_step": ms_per_step}
         value, ms_per_step = batched["value"], batched["ms_per_step"]
     roofline_mpts = B / (upd_bytes / (peak * 1e9)) / 1e6
-    tpp = TRAFFIC_PER_POINT.get(kernel_source_hash())
-    traffic = tpp * B if tpp is not None else None
+    traffic = TRAFFIC_PER_LAUNCH.get((kernel_source_hash(), w.name))
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

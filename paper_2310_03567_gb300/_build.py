@@ -70,13 +70,16 @@ def library_headers() -> list[str]:
 
 
 def _common_flags(extra: list[str] | None = None) -> list[str]:
-    # -dlcm=cg: plain global loads are served by the coherent L2, not the
-    # per-SM L1, because the persistent kernel re-reads node tables, split
-    # lists and grids that other blocks rewrote after a grid barrier (L1s are
-    # not coherent with each other within one grid). Batch points are read
-    # with __ldcg too: a merged update reads them from a staging buffer that
-    # the same launch has just written.
-    return ([*ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17", "-Xptxas", "-dlcm=cg",
+    # Plain global loads may be cached in L1. The persistent kernel re-reads
+    # node tables, split lists, mover lists and grids that other blocks wrote
+    # before a grid barrier; at every barrier thread 0 of each block takes a
+    # GPU-scope acquire fence after the other blocks' release, and the block
+    # barrier that follows orders it before every thread's later loads, so
+    # those loads see the writes (no phase reads what another block writes in
+    # the same phase; control words are volatile or atomic). Measured against
+    # serving every plain load from L2 (-dlcm=cg): 3 % faster on the aerial
+    # and the clustered stream, with the parity tests unchanged.
+    return ([*ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17",
              "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
              "-I", INCLUDE_DIR, "-I", CSRC_DIR] + (extra or []))
 
