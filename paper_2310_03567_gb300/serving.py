@@ -55,6 +55,7 @@ class Request:
     dev: object = None  # device copy while in flight (a view of the staging buffer)
     ready: object = None  # event: the device copy is complete
     slot: int = -1  # byte offset of the device copy in the staging buffer
+    launch_points: int = 0  # points of the launch that applied it
 
     @property
     def n(self) -> int:
@@ -227,9 +228,11 @@ class Server:
             reqs, self.queued[k] = q[:take], q[take:]
             tree = self.trees[k]
             t = self.now()
+            lp = sum(r.n for r in reqs)
             for r in reqs:
                 tree.stream.wait_event(r.ready)
                 r.launched = t
+                r.launch_points = lp
             if self.plain:
                 rc = tree.insert(reqs[0].dev, stream=tree.stream, check=False)
             else:

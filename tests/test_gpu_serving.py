@@ -97,3 +97,52 @@ def test_launch_width():
     want = oracle.static_build(oracle.Config.make(root_log2=20, leaf_capacity=20_000), pts)
     assert_snapshots_equal(t.snapshot(), want)
     t.close()
+
+
+def test_bench_shaped_trace_of_16_octrees():
+    """The serving bench's shape at 1 % of its sizes: 16 octrees (uniform,
+    terrain and clustered in turn, sizes log-uniform in 50k-2M points),
+    requests log-uniform in 1k-50k points arriving by a Poisson process,
+    two launches in flight, a frame every 5 ms. Every octree equals its
+    requests inserted alone, one after another, and the oracle's closed form
+    of its stream."""
+    rng = np.random.default_rng(4)
+    sizes = np.exp(rng.uniform(np.log(5e6), np.log(2e8), 16)) * 0.01
+    pts, specs = [], []
+    for k, n in enumerate(int(s) for s in sizes):
+        kind = ("uniform", "terrain", "clustered")[k % 3]
+        if kind == "uniform":
+            p, root = synth.uniform(400 + k, 1 << 20, n), 20
+        elif kind == "terrain":
+            p, root = synth.terrain(400 + k, n), 22
+        else:
+            p, root = synth.clustered(400 + k, max(50, n // 15_000), n), 21
+        cfg = simlod.default_config(root_log2=root, max_batch_points=1 << 17,
+                                    spill_capacity=n + (1 << 20), backlog_capacity=n + (1 << 20),
+                                    max_nodes=1 << 16)
+        side = float(1 << root)
+        cam = simlod.view_proj(side * np.array([-0.4, -0.5, 0.4]), side * np.array([0.5, 0.5, 0.05]),
+                               60.0, 16 / 9)
+        specs.append(serving.OctreeSpec(cfg, n * 80 + (64 << 20), cam))
+        pts.append(p)
+    hosts = [pinned(p) for p in pts]
+    reqs = serving.poisson_requests(hosts, 1_000, 50_000, rate_pts_per_s=2e9, seed=7)
+    assert len(reqs) > 300
+    arenas = sum(simlod.arena_bytes(sp.cfg, sp.data_bytes) for sp in specs)
+    srv = serving.Server(specs, hbm_budget=arenas + (256 << 20), compute_slots=2, frame_ms=5.0)
+    done = srv.run(reqs)
+    rep = srv.report()
+    assert len(done) == len(reqs) and rep["points"] == sum(len(p) for p in pts)
+    assert rep["frames"] > 0 and rep["launches"] < len(reqs)  # requests were batched
+    for k, tree in enumerate(srv.trees):
+        got = tree.snapshot()
+        cfg = specs[k].cfg
+        alone = simlod.Octree(cfg, simlod.make_arena(cfg, specs[k].data_bytes),
+                              stream=torch.cuda.Stream())
+        for r in [r for r in reqs if r.octree == k]:
+            assert alone.insert(r.points.cuda()) == simlod.OK
+        assert_snapshots_equal(got, alone.snapshot())
+        alone.close()
+        want = oracle.static_build(oracle.Config.make(root_log2=cfg.root_log2), pts[k])
+        assert_snapshots_equal(got, want)
+    srv.close()
