@@ -58,7 +58,11 @@ def update_alg_bytes(B, S, V, K, grid_bytes):
 # it has been captured again.
 KERNEL_SOURCES = ("paper_2310_03567_gb300/csrc/device.cuh", "paper_2310_03567_gb300/csrc/fused.cuh",
                   "include/simlod.h", "paper_2310_03567_gb300/_build.py")
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    # clustered-300M, one launch over its 54 batches: 38.98 GB read + 23.29 GB
+    # written in 51.72 ms (profiles/k_fused_clustered300m_dram.md)
+    ("aba259267234b2d8", "clustered-300000000"): 62.27e9,
+}
 
 
 def kernel_source_hash():
@@ -508,18 +512,23 @@ def run_ours(args):
         copy_stream.wait_stream(stream)  # the next step's copies overwrite this one's input
         return tree.stats()
 
-    e2e_steps = max(1, min(args.steps, 3))
-    e2e_times = {}
+    # every step is timed on its own (each ends with the stats read, so the
+    # device is idle between steps); a mode's time is its median step
+    e2e_steps = max(3, min(args.steps, 5))
+    e2e_times, e2e_step_ms = {}, {}
     for name, fn in (("copy_then_update", e2e_step), ("pipelined", e2e_pipelined_step),
                      ("direct", e2e_direct_step), ("host_fed", e2e_host_fed_step)):
         fn()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        steps_s = []
         for _ in range(e2e_steps):
+            t0 = time.perf_counter()
             st_e2e = fn()
-        e2e_times[name] = (time.perf_counter() - t0) / e2e_steps
-        if st_e2e["points"] != n_points:
-            raise RuntimeError(f"e2e {name}: {st_e2e['points']} points applied")
+            steps_s.append(time.perf_counter() - t0)
+            if st_e2e["points"] != n_points:
+                raise RuntimeError(f"e2e {name}: {st_e2e['points']} points applied")
+        e2e_times[name] = statistics.median(steps_s)
+        e2e_step_ms[name] = [round(x * 1e3, 2) for x in steps_s]
     e2e_mode = min(e2e_times, key=e2e_times.get)
     e2e_s = e2e_times[e2e_mode]
     del host_pts, dev_e2e, host_parts, ready
@@ -604,7 +613,9 @@ def run_ours(args):
                 "h2d_bytes_per_step": n_points * 16 + 24 * len(ptrs)
                 + (4 * len(ptrs) if e2e_mode == "host_fed" else 0),
                 "d2h_bytes_per_step": CTL_BYTES, "mode": e2e_mode,
-                "modes_mpts": {k: n_points / v / 1e6 for k, v in e2e_times.items()}},
+                "timing": f"median of {e2e_steps} steps, each from the host's clock",
+                "modes_mpts": {k: n_points / v / 1e6 for k, v in e2e_times.items()},
+                "modes_step_ms": e2e_step_ms},
         "clocks": clk,
     }
     if batched is not None:
