@@ -111,3 +111,66 @@ def test_only_idle_nodes_are_compacted():
     want = oracle.static_build(oracle.Config.make(root_log2=22), w.points)
     assert_snapshots_equal(tree.snapshot(), want)
     tree.close()
+
+
+def test_compaction_with_small_chunks_and_unsplittable_leaves():
+    """Chunks of 3 records, leaves of at most 40 points, and a one-unit cube
+    holding 500 copies of one point (a leaf that can never split and outgrows
+    its directory): compaction and the inserts after it, plain and fused,
+    keep the oracle's octree at every step."""
+    kw = dict(root_log2=10, leaf_capacity=40, chunk_points=3, grid_log2=4)
+    cfg = simlod.default_config(max_batch_points=1 << 16, spill_capacity=1 << 17,
+                                backlog_capacity=1 << 17, max_nodes=1 << 16, **kw)
+    tree = simlod.Octree(cfg, simlod.make_arena(cfg, 256 << 20), stream=torch.cuda.Stream())
+    ocfg = oracle.Config.make(**kw)
+    ref = oracle.Incremental(ocfg)
+    rng = np.random.default_rng(21)
+    pts = synth.uniform(22, 1 << 10, 6000)
+    dup = np.repeat(pts[:1], 500)
+    dup["r"] = np.arange(500) % 256
+    stream = np.concatenate([pts[:2000], dup, pts[2000:]])
+    cuts = [0, 700, 2500, 3100, 4000, 5200, 6500]
+    for k in range(len(cuts) - 1):
+        b = stream[cuts[k]:cuts[k + 1]]
+        if k % 2:
+            tree.insert_many([simlod.points_tensor(b)])
+            assert tree.sync() == simlod.OK
+        else:
+            assert tree.insert(simlod.points_tensor(b)) == simlod.OK
+        assert ref.insert(b) == oracle.OK
+        tree.compact(int(rng.integers(0, 2)))
+        assert tree.sync() == simlod.OK
+        got = tree.snapshot()
+        assert_snapshots_equal(got, ref.snapshot())
+        check_allocator(got, tree.stats())
+    st = tree.stats()
+    assert st["compacted_total"] > 0 and st["decompacted_total"] > 0
+    ref.close()
+    tree.close()
+
+
+def test_compaction_without_room_changes_nothing():
+    """A data region with almost no room left: the nodes that do not fit stay
+    chunk lists, nothing fails, and the octree is unchanged."""
+    w = synth.aerial_workload(n=1_000_000, batch=250_000)
+    cfg = simlod.default_config(root_log2=22, max_batch_points=1 << 18, spill_capacity=1 << 21,
+                                backlog_capacity=1 << 21, max_nodes=1 << 16)
+    # the data region for these points with little to spare (found by trying)
+    for data in (40 << 20, 48 << 20, 64 << 20, 96 << 20):
+        tree = simlod.Octree(cfg, simlod.make_arena(cfg, data), stream=torch.cuda.Stream())
+        ok = all(tree.insert(simlod.points_tensor(b), check=False) == simlod.OK
+                 for b in w.batches())
+        if ok:
+            break
+        tree.close()
+    assert ok
+    before = tree.snapshot()
+    st0 = tree.stats()
+    tree.compact(0)
+    assert tree.sync() == simlod.OK
+    st = tree.stats()
+    assert st["data_used"] <= st["data_bytes"]
+    assert_snapshots_equal(tree.snapshot(), before)
+    check_allocator(tree.snapshot(), st)
+    assert st["compact_nodes"] <= st0["nodes"]
+    tree.close()
