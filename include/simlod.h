@@ -305,6 +305,19 @@ SIMLOD_API int simlod_variant_info(uint32_t variant, simlod_variant_desc* out);
 SIMLOD_API int simlod_set_launch_width(simlod_t* h, uint32_t blocks_per_sm,
                                        uint32_t* max_blocks_per_sm);
 
+/* Progress of the handle's persistent launches (simlod_insert_batches,
+ * simlod_insert_batches_host, simlod_frame_update; not the batched form's
+ * plans, nor the plain form): *finished = batches those launches have
+ * finished (applied or rejected) since create, *submitted = batches handed to
+ * them (both counted modulo 2^32); the k-th batch handed over (from 0) is
+ * finished once *finished > k.
+ * The kernel writes the count into page-locked host memory after each batch,
+ * so the call only reads it: it neither waits nor synchronises, and may be
+ * made while a launch runs (the serving form completes each request when its
+ * own batch is finished). Not in the paper: its update kernel has no caller
+ * that needs a request's completion before the whole frame's. */
+SIMLOD_API int simlod_progress(simlod_t* h, uint64_t* finished, uint64_t* submitted);
+
 /* Time limits of the waits inside the handle's persistent launches (not in
  * the paper, whose kernel waits without a limit): barrier_ns bounds one
  * block's wait at a grid barrier, ready_ns one wait for a batch's ready flag

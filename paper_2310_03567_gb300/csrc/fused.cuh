@@ -259,6 +259,11 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
     if (tid == 0) {
       f->consumed = b + 1;
       if (budget_ns != NO_BUDGET && globaltimer_ns() - t_begin > budget_ns) f->stop = 1;
+      if (c.progress) {  // batch b is applied (or rejected): tell the host
+        const unsigned int done = c.progress_base + b + 1u;
+        asm volatile("st.release.sys.global.u32 [%0], %1;" : : "l"(c.progress), "r"(done)
+                     : "memory");
+      }
     }
     if (!grid_barrier(c, f)) return;
     clk.tick(c, PH_END);

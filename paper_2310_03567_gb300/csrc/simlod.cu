@@ -282,6 +282,9 @@ struct simlod {
   cudaEvent_t desc_done;    // the last batch-table copy has finished
   FusedCtl* fctl_host;      // pinned mirror of the fused control words
   uint32_t* one_host;       // pinned word holding 1: the source of ready-flag copies
+  uint32_t* prog_host;      // mapped pinned word: batches of persistent launches finished
+  uint32_t* prog_dev;       //   its device address
+  uint32_t prog_submitted;  // batches handed to persistent launches (simlod_progress)
   cudaEvent_t flags_clear;  // the ready flags of the last host-fed launch are cleared
   FusedCtl* fctl_dev;
   BatchDesc* batches_dev;
@@ -449,6 +452,8 @@ void make_ctx(simlod_t* h) {
   c.mv_cap = g.max_batch_points + g.spill_capacity;
   c.bar_ns = FUSED_BARRIER_NS;
   c.ready_ns = FUSED_READY_NS;
+  c.progress = nullptr;  // set per persistent launch (launch_fused)
+  c.progress_base = 0;
 }
 
 int error_from_bits(uint32_t e) {
@@ -640,6 +645,8 @@ int launch_fused(simlod_t* h, const simlod_point* const* d_batches, const uint64
       cudaMemsetAsync(h->fctl_dev, 0, sizeof(FusedCtl), s) != cudaSuccess)
     return poison(h, SIMLOD_ERR_CUDA);
   Ctx c = h->ctx;
+  c.progress = h->prog_dev;
+  c.progress_base = h->prog_submitted;
   const BatchDesc* bt = h->batches_dev;
   FusedCtl* f = h->fctl_dev;
   uint32_t max_iters = h->cfg.max_expand_iters ? h->cfg.max_expand_iters : h->cfg.root_log2 + 1;
@@ -654,6 +661,7 @@ int launch_fused(simlod_t* h, const simlod_point* const* d_batches, const uint64
   if (rc || le != cudaSuccess) return poison(h, SIMLOD_ERR_CUDA);
   h->base += total;  // upper bound until the next control-block read
   h->mirror_stale = true;
+  h->prog_submitted += n;
   return SIMLOD_OK;
 }
 
@@ -787,6 +795,16 @@ SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t are
     return SIMLOD_ERR_CUDA;
   }
   *h->one_host = 1u;
+  // progress of persistent launches: a word the kernel writes in host memory
+  if (cudaHostAlloc(reinterpret_cast<void**>(&h->prog_host), sizeof(uint32_t),
+                    cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->prog_dev), h->prog_host, 0) !=
+          cudaSuccess) {
+    simlod_destroy(h);
+    return SIMLOD_ERR_CUDA;
+  }
+  *h->prog_host = 0u;
+  h->prog_submitted = 0u;
   // the arena is the caller's memory: start from a zeroed control block
   if (cudaMemsetAsync(h->ctx.ctl, 0, sizeof(Ctl), static_cast<cudaStream_t>(stream)) !=
       cudaSuccess) {
@@ -891,7 +909,10 @@ SIMLOD_API int simlod_frame_update(simlod_t* h, const simlod_point* const* d_bat
   const unsigned long long budget = budget_ns >= NO_BUDGET ? NO_BUDGET - 1 : budget_ns;
   int rc = launch_fused(h, d_batches, counts, n_batches, budget, static_cast<cudaStream_t>(stream));
   if (rc) return rc;
-  return finish_fused(h, consumed);
+  rc = finish_fused(h, consumed);
+  // the batches past the budget were not handed over: the caller passes them again
+  h->prog_submitted -= n_batches - std::min(*consumed, n_batches);
+  return rc;
 }
 
 // ------------------------------------------------------------ batched form
@@ -1194,6 +1215,13 @@ SIMLOD_API int simlod_set_launch_width(simlod_t* h, uint32_t blocks_per_sm,
   if (blocks_per_sm > (uint32_t)h->fused_max_per_sm) return SIMLOD_ERR_INVALID_ARG;
   const int bps = blocks_per_sm ? (int)blocks_per_sm : h->fused_max_per_sm;
   h->fused_grid = bps * h->sm_count;
+  return SIMLOD_OK;
+}
+
+SIMLOD_API int simlod_progress(simlod_t* h, uint64_t* finished, uint64_t* submitted) {
+  if (!h || !finished) return SIMLOD_ERR_INVALID_ARG;
+  *finished = *reinterpret_cast<volatile uint32_t*>(h->prog_host);
+  if (submitted) *submitted = h->prog_submitted;
   return SIMLOD_OK;
 }
 
@@ -1651,6 +1679,7 @@ SIMLOD_API int simlod_destroy(simlod_t* h) {
   if (h->desc_host) cudaFreeHost(h->desc_host);
   if (h->fctl_host) cudaFreeHost(h->fctl_host);
   if (h->one_host) cudaFreeHost(h->one_host);
+  if (h->prog_host) cudaFreeHost(h->prog_host);
   if (h->desc_done) cudaEventDestroy(h->desc_done);
   if (h->flags_clear) cudaEventDestroy(h->flags_clear);
   delete h;

@@ -10,7 +10,7 @@ request (points of one octree, in pinned host memory) is admitted, in arrival
 order, when its device copy fits a free range of that buffer; it is copied on
 the server's copy stream, so that the copy overlaps the launches running on
 its octree's stream, and the launch that applies it waits for the copy's
-event. Its range is freed when the launch that read it has finished.
+event. Its range is freed when its batch has been applied.
 When a launch slot is free, the octree with the oldest
 admitted request gets one fused launch (simlod_insert_batches) over its
 admitted requests, each request one batch, in arrival order, up to
@@ -25,6 +25,11 @@ that is due holds new launches back until the launches in flight have
 finished and renders alone: render blocks that took SM slots beside one
 persistent launch would hold back the next persistent launch, which needs a
 slot on every SM.
+
+A request of the serving form completes when its own batch of the launch is
+finished (the library's progress count, which the persistent kernel writes
+into host memory after every batch), not when the whole launch ends; its
+staging range is freed then too.
 
 Requests of one octree are applied in arrival order, which fixes their gidx:
 each octree ends up exactly as if its requests had been inserted alone, one
@@ -155,12 +160,13 @@ class Server:
         self.copy_stream = torch.cuda.Stream()
         self.pending = []      # arrived, not admitted (arrival order)
         self.queued = [[] for _ in self.trees]   # admitted, not launched, per octree
-        self.inflight = []     # (event, octree, requests)
+        self.inflight = []     # (event, octree, requests, progress count before the launch)
         self.busy = [False] * len(self.trees)
         self.finished = []
         self.frame_times = []
         self.frame_waits = []
         self.launches = 0
+        self.early = 0         # requests completed before the end of their launch
         self.t0 = None
 
     def reset(self):
@@ -176,6 +182,7 @@ class Server:
         self.finished, self.frame_times, self.frame_waits = [], [], []
         self.busy = [False] * len(self.trees)
         self.launches = 0
+        self.early = 0         # requests completed before the end of their launch
         self.t0 = None
 
     # ------------------------------------------------------------- clock
@@ -183,20 +190,35 @@ class Server:
         return time.perf_counter() - self.t0
 
     # ------------------------------------------------------------ phases
+    def _complete(self, r, t):
+        r.done = t
+        r.dev = r.ready = None
+        self.pool.release(r.slot, r.nbytes)
+        r.slot = -1
+        self.finished.append(r)
+
     def _poll(self):
         keep = []
-        for ev, k, reqs in self.inflight:
+        for ev, k, reqs, base in self.inflight:
             if ev.query():
                 t = self.now()
                 for r in reqs:
-                    r.done = t
-                    r.dev = r.ready = None
-                    self.pool.release(r.slot, r.nbytes)
-                    r.slot = -1
-                    self.finished.append(r)
+                    if r.done < 0:
+                        self._complete(r, t)
                 self.busy[k] = False
-            else:
-                keep.append((ev, k, reqs))
+                continue
+            if base is not None:
+                # a persistent launch applies its requests one by one: each
+                # completes (and frees its staging range) when its own batch
+                # is finished, before the launch ends
+                done = (self.trees[k].progress()[0] - base) & 0xFFFFFFFF
+                t = None
+                for r in reqs[:min(done, len(reqs))]:
+                    if r.done < 0:
+                        t = self.now() if t is None else t
+                        self._complete(r, t)
+                        self.early += 1
+            keep.append((ev, k, reqs, base))
         self.inflight = keep
 
     def _admit(self):
@@ -233,15 +255,17 @@ class Server:
                 tree.stream.wait_event(r.ready)
                 r.launched = t
                 r.launch_points = lp
+            base = None
             if self.plain:
                 rc = tree.insert(reqs[0].dev, stream=tree.stream, check=False)
             else:
+                base = tree.progress()[1]  # batches handed to this handle's launches so far
                 rc = tree.insert_many_ptrs([r.dev.data_ptr() for r in reqs], [r.n for r in reqs])
             if rc != simlod.OK:
                 raise simlod.SimlodError(rc, "insert")
             ev = torch.cuda.Event()
             ev.record(tree.stream)
-            self.inflight.append((ev, k, reqs))
+            self.inflight.append((ev, k, reqs, base))
             self.busy[k] = True
             self.launches += 1
 
@@ -336,7 +360,8 @@ class Server:
                                    "p99": float(np.percentile(queue, 99))},
                 "service_ms": {"p50": float(np.percentile(service, 50)),
                                "p99": float(np.percentile(service, 99))},
-                "launches": self.launches, "frames": len(self.frame_times),
+                "launches": self.launches, "completed_before_launch_end": self.early,
+                "frames": len(self.frame_times),
                 "frame_ms": {"p50": float(np.percentile(ft, 50)),
                              "p99": float(np.percentile(ft, 99))},
                 "frame_wait_ms": {"p50": float(np.percentile(fw, 50)),

@@ -135,6 +135,7 @@ SIGNATURES = {
     "simlod_plan_autotune": (_I32, [_P, _P, _P, _U32, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     "simlod_variant_info": (_I32, [_U32, _P]),
     "simlod_compact": (_I32, [_P, _U32, _P]),
+    "simlod_progress": (_I32, [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
 }
 
 
@@ -475,6 +476,15 @@ class Octree:
         if rc != OK:
             raise SimlodError(rc, "simlod_set_launch_width")
         return int(mx.value)
+
+    def progress(self) -> tuple[int, int]:
+        """(batches finished, batches submitted) of this handle's persistent
+        launches; reads host memory only (simlod_progress)."""
+        fin, sub = ctypes.c_uint64(), ctypes.c_uint64()
+        rc = self._lib.simlod_progress(self._h, ctypes.byref(fin), ctypes.byref(sub))
+        if rc != OK:
+            raise SimlodError(rc, "simlod_progress")
+        return int(fin.value), int(sub.value)
 
     def compact(self, idle_updates: int = 0, stream=None) -> None:
         """Turn the chunk lists of nodes idle for idle_updates updates into

@@ -352,3 +352,41 @@ def test_grid_barrier_times_out_with_every_block_present():
     assert t.sync() == simlod.OK
     assert_snapshots_equal(t.snapshot(),
                            oracle.static_build(oracle.Config.make(root_log2=22), w.points))
+
+
+def test_progress_counts_finished_batches():
+    """simlod_progress: the persistent launch counts the batches it has
+    finished in host memory. The count rises batch by batch while a launch
+    runs and reaches the batches handed over when it ends; a rejected batch
+    counts as finished; batches that a frame budget left out are not counted
+    as handed over; plain inserts change neither count."""
+    import time
+    kw = dict(root_log2=16, leaf_capacity=500, chunk_points=50, grid_log2=6)
+    pts = synth.uniform(51, 1 << 16, 300_000)
+    t = make_tree(512 << 20, **caps(**kw))
+    assert t.progress() == (0, 0)
+    ts = [simlod.points_tensor(pts[k:k + 5_000]) for k in range(0, 200_000, 5_000)]
+    torch.cuda.synchronize()
+    t.insert_many(ts)
+    seen, deadline = [], time.perf_counter() + 60.0
+    while time.perf_counter() < deadline:
+        fin, sub = t.progress()
+        seen.append(fin)
+        if fin == sub:
+            break
+    assert t.sync() == simlod.OK
+    assert t.progress() == (40, 40) and seen[-1] == 40
+    assert all(a <= b for a, b in zip(seen, seen[1:]))
+    assert len(set(seen)) >= 3  # counts between 0 and 40 were seen while the launch ran
+    bad = pts[200_000:201_000].copy()
+    bad[7] = (200_000, 1, 1, 0, 0, 0, 0)
+    rc = fused_insert(t, [pts[201_000:210_000], bad, pts[210_000:220_000]])
+    assert rc == simlod.ERR_OUT_OF_BOUNDS and t.sync() == simlod.OK
+    assert t.progress() == (43, 43)
+    rest = [simlod.points_tensor(pts[k:k + 10_000]) for k in range(220_000, 260_000, 10_000)]
+    rc, used = t.frame_update(rest, budget_ns=0)
+    assert rc == simlod.OK and used == 1 and t.progress() == (44, 44)
+    assert t.insert(simlod.points_tensor(pts[230_000:])) == simlod.OK
+    assert t.progress() == (44, 44)
+    want = np.concatenate([pts[:200_000], pts[201_000:230_000], pts[230_000:]])
+    assert_snapshots_equal(t.snapshot(), oracle.static_build(ocfg(**kw), want))

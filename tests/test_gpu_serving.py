@@ -55,7 +55,10 @@ def test_served_octrees_equal_alone_and_oracle(budget_mb, slots, frame_ms, rate)
     done = srv.run(reqs)
     rep = srv.report()
     assert len(done) == len(reqs) and rep["points"] == sum(len(p) for p in pts)
-    assert all(r.done >= r.admitted >= r.arrival for r in done)
+    assert all(r.done >= r.launched >= r.admitted >= r.arrival for r in done)
+    for k in range(len(specs)):  # one octree's requests complete in arrival order
+        mine = [r for r in reqs if r.octree == k]
+        assert all(a.done <= b.done for a, b in zip(mine, mine[1:]))
     if budget_mb:
         assert rep["admission_wait_ms"]["p99"] > 0.0
     if frame_ms:
