@@ -167,6 +167,7 @@ class Server:
         self.frame_waits = []
         self.launches = 0
         self.early = 0         # requests completed before the end of their launch
+        self.gaps = []         # seconds between the starts of consecutive scheduler iterations
         self.t0 = None
 
     def reset(self):
@@ -183,6 +184,7 @@ class Server:
         self.busy = [False] * len(self.trees)
         self.launches = 0
         self.early = 0         # requests completed before the end of their launch
+        self.gaps = []         # seconds between the starts of consecutive scheduler iterations
         self.t0 = None
 
     # ------------------------------------------------------------- clock
@@ -310,8 +312,12 @@ class Server:
         nxt = 0
         next_frame = self.frame_ms / 1e3 if self.frame_ms else None
         frame_evs, frame_t, due_t = [], 0.0, None
+        t_prev = None
         while nxt < len(reqs) or self.pending or any(self.queued) or self.inflight:
             t = self.now()
+            if t_prev is not None:
+                self.gaps.append(t - t_prev)
+            t_prev = t
             while nxt < len(reqs) and reqs[nxt].arrival <= t:
                 self.pending.append(reqs[nxt])
                 nxt += 1
@@ -350,6 +356,7 @@ class Server:
         fw = np.array(self.frame_waits) * 1e3 if self.frame_waits else np.zeros(1)
         queue = np.array([r.launched - r.admitted for r in self.finished]) * 1e3
         service = np.array([r.done - r.launched for r in self.finished]) * 1e3
+        gaps = np.array(self.gaps) * 1e3 if self.gaps else np.zeros(1)
         return {"requests": len(self.finished), "points": pts, "seconds": span,
                 "mpts_per_s": pts / span / 1e6 if span > 0 else 0.0,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)),
@@ -360,6 +367,9 @@ class Server:
                                    "p99": float(np.percentile(queue, 99))},
                 "service_ms": {"p50": float(np.percentile(service, 50)),
                                "p99": float(np.percentile(service, 99))},
+                "scheduler_gap_ms": {"p50": float(np.percentile(gaps, 50)),
+                                     "p99": float(np.percentile(gaps, 99)),
+                                     "max": float(gaps.max())},
                 "launches": self.launches, "completed_before_launch_end": self.early,
                 "frames": len(self.frame_times),
                 "frame_ms": {"p50": float(np.percentile(ft, 50)),
