@@ -306,16 +306,19 @@ SIMLOD_API int simlod_set_launch_width(simlod_t* h, uint32_t blocks_per_sm,
                                        uint32_t* max_blocks_per_sm);
 
 /* Progress of the handle's persistent launches (simlod_insert_batches,
- * simlod_insert_batches_host, simlod_frame_update; not the batched form's
- * plans, nor the plain form): *finished = batches those launches have
- * finished (applied or rejected) since create, *submitted = batches handed to
- * them (both counted modulo 2^32); the k-th batch handed over (from 0) is
- * finished once *finished > k.
- * The kernel writes the count into page-locked host memory after each batch,
- * so the call only reads it: it neither waits nor synchronises, and may be
- * made while a launch runs (the serving form completes each request when its
- * own batch is finished). Not in the paper: its update kernel has no caller
- * that needs a request's completion before the whole frame's. */
+ * simlod_insert_batches_host, simlod_insert_batches_budget,
+ * simlod_frame_update; not the batched form's plans, nor the plain form):
+ * *finished = batches those launches have finished (applied or rejected)
+ * since create; *submitted = batches handed to them, less the batches that a
+ * budget stop dropped (both counted modulo 2^32). Batches finish in the order
+ * they were handed over, so a launch that started with *finished = f0 has
+ * finished its first k batches once *finished >= f0 + k; when a budget stop
+ * ends it early, *finished - f0 after the launch is the number it applied.
+ * The kernel writes both counts into page-locked host memory after each
+ * batch, so the call only reads them: it neither waits nor synchronises, and
+ * may be made while a launch runs (the serving form completes each request
+ * when its own batch is finished). Not in the paper: its update kernel has
+ * no caller that needs a request's completion before the whole frame's. */
 SIMLOD_API int simlod_progress(simlod_t* h, uint64_t* finished, uint64_t* submitted);
 
 /* Time limits of the waits inside the handle's persistent launches (not in
@@ -336,6 +339,19 @@ SIMLOD_API int simlod_set_wait_limits(simlod_t* h, uint64_t barrier_ns, uint64_t
 SIMLOD_API int simlod_frame_update(simlod_t* h, const simlod_point* const* d_batches,
                                    const uint64_t* counts, uint32_t n_batches,
                                    uint64_t budget_ns, void* stream, uint32_t* consumed);
+
+/* Frame-budget update without the wait: as simlod_frame_update (batch k > 0
+ * starts only while the launch has run for at most budget_ns on the GPU's
+ * global timer; batches are never cut), but asynchronous like
+ * simlod_insert_batches. The batches after the stop are dropped: the caller
+ * learns how many were applied from simlod_progress once `stream` has passed
+ * the launch, and passes the rest again. d_batches[k] must stay valid until
+ * then. Rejections and errors as in simlod_insert_batches. (The serving form
+ * gives a launch the time left before the next frame is due, so that the
+ * frame does not wait for the rest of a long launch.) */
+SIMLOD_API int simlod_insert_batches_budget(simlod_t* h, const simlod_point* const* d_batches,
+                                            const uint64_t* counts, uint32_t n_batches,
+                                            uint64_t budget_ns, void* stream);
 
 /* Empty the octree (one empty root leaf, gidx counter 0) without touching
  * the arena allocation; the handle's poison is cleared. Enqueued on `stream`

@@ -247,8 +247,8 @@ struct Ctx {
   unsigned long long* launch_bar;  // barrier word of the persistent launch (abort bit)
   unsigned long long bar_ns;       // persistent launch: time limit of one grid-barrier wait
   unsigned long long ready_ns;     //   and of one wait for a batch's ready flag
-  unsigned int* progress;          // persistent launch: host-mapped count of finished batches
-  unsigned int progress_base;      //   batches of earlier launches (nullptr: not reported)
+  unsigned int* progress;          // persistent launch: host-mapped words, [0] batches finished,
+                                   //   [1] batches dropped by budget stops (nullptr: none)
 };
 
 // Abort bit of a persistent launch's barrier word: set with the first

@@ -258,10 +258,26 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
     }
     if (tid == 0) {
       f->consumed = b + 1;
-      if (budget_ns != NO_BUDGET && globaltimer_ns() - t_begin > budget_ns) f->stop = 1;
-      if (c.progress) {  // batch b is applied (or rejected): tell the host
-        const unsigned int done = c.progress_base + b + 1u;
-        asm volatile("st.release.sys.global.u32 [%0], %1;" : : "l"(c.progress), "r"(done)
+      const bool stop = budget_ns != NO_BUDGET && globaltimer_ns() - t_begin > budget_ns;
+      if (stop) f->stop = 1;
+      if (c.progress) {
+        // the host's counts: only this handle's launches write them, and they
+        // run one after another, so thread 0 adds to them by load and store
+        if (stop && b + 1u < nb) {
+          // the batches after b are dropped for good
+          unsigned int d;
+          asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(d) : "l"(c.progress + 1)
+                       : "memory");
+          d += nb - b - 1u;
+          asm volatile("st.relaxed.sys.global.u32 [%0], %1;" : : "l"(c.progress + 1), "r"(d)
+                       : "memory");
+        }
+        // batch b is applied (or rejected); the release also publishes the
+        // dropped count above
+        unsigned int done;
+        asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(done) : "l"(c.progress)
+                     : "memory");
+        asm volatile("st.release.sys.global.u32 [%0], %1;" : : "l"(c.progress), "r"(done + 1u)
                      : "memory");
       }
     }

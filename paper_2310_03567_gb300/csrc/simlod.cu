@@ -282,8 +282,8 @@ struct simlod {
   cudaEvent_t desc_done;    // the last batch-table copy has finished
   FusedCtl* fctl_host;      // pinned mirror of the fused control words
   uint32_t* one_host;       // pinned word holding 1: the source of ready-flag copies
-  uint32_t* prog_host;      // mapped pinned word: batches of persistent launches finished
-  uint32_t* prog_dev;       //   its device address
+  uint32_t* prog_host;      // mapped pinned words: [0] batches of persistent launches
+  uint32_t* prog_dev;       //   finished, [1] batches dropped by budget stops; device address
   uint32_t prog_submitted;  // batches handed to persistent launches (simlod_progress)
   cudaEvent_t flags_clear;  // the ready flags of the last host-fed launch are cleared
   FusedCtl* fctl_dev;
@@ -453,7 +453,6 @@ void make_ctx(simlod_t* h) {
   c.bar_ns = FUSED_BARRIER_NS;
   c.ready_ns = FUSED_READY_NS;
   c.progress = nullptr;  // set per persistent launch (launch_fused)
-  c.progress_base = 0;
 }
 
 int error_from_bits(uint32_t e) {
@@ -646,7 +645,6 @@ int launch_fused(simlod_t* h, const simlod_point* const* d_batches, const uint64
     return poison(h, SIMLOD_ERR_CUDA);
   Ctx c = h->ctx;
   c.progress = h->prog_dev;
-  c.progress_base = h->prog_submitted;
   const BatchDesc* bt = h->batches_dev;
   FusedCtl* f = h->fctl_dev;
   uint32_t max_iters = h->cfg.max_expand_iters ? h->cfg.max_expand_iters : h->cfg.root_log2 + 1;
@@ -796,14 +794,14 @@ SIMLOD_API int simlod_create(const simlod_config* cfg, void* d_arena, size_t are
   }
   *h->one_host = 1u;
   // progress of persistent launches: a word the kernel writes in host memory
-  if (cudaHostAlloc(reinterpret_cast<void**>(&h->prog_host), sizeof(uint32_t),
+  if (cudaHostAlloc(reinterpret_cast<void**>(&h->prog_host), 2 * sizeof(uint32_t),
                     cudaHostAllocMapped) != cudaSuccess ||
       cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->prog_dev), h->prog_host, 0) !=
           cudaSuccess) {
     simlod_destroy(h);
     return SIMLOD_ERR_CUDA;
   }
-  *h->prog_host = 0u;
+  h->prog_host[0] = h->prog_host[1] = 0u;
   h->prog_submitted = 0u;
   // the arena is the caller's memory: start from a zeroed control block
   if (cudaMemsetAsync(h->ctx.ctl, 0, sizeof(Ctl), static_cast<cudaStream_t>(stream)) !=
@@ -909,10 +907,18 @@ SIMLOD_API int simlod_frame_update(simlod_t* h, const simlod_point* const* d_bat
   const unsigned long long budget = budget_ns >= NO_BUDGET ? NO_BUDGET - 1 : budget_ns;
   int rc = launch_fused(h, d_batches, counts, n_batches, budget, static_cast<cudaStream_t>(stream));
   if (rc) return rc;
-  rc = finish_fused(h, consumed);
-  // the batches past the budget were not handed over: the caller passes them again
-  h->prog_submitted -= n_batches - std::min(*consumed, n_batches);
-  return rc;
+  return finish_fused(h, consumed);
+}
+
+SIMLOD_API int simlod_insert_batches_budget(simlod_t* h, const simlod_point* const* d_batches,
+                                            const uint64_t* counts, uint32_t n_batches,
+                                            uint64_t budget_ns, void* stream) {
+  if (!h || (n_batches && (!d_batches || !counts)) || n_batches > MAX_FUSED_BATCHES)
+    return SIMLOD_ERR_INVALID_ARG;
+  if (h->sticky) return SIMLOD_ERR_POISONED;
+  if (n_batches == 0) return SIMLOD_OK;
+  const unsigned long long budget = budget_ns >= NO_BUDGET ? NO_BUDGET - 1 : budget_ns;
+  return launch_fused(h, d_batches, counts, n_batches, budget, static_cast<cudaStream_t>(stream));
 }
 
 // ------------------------------------------------------------ batched form
@@ -1220,8 +1226,12 @@ SIMLOD_API int simlod_set_launch_width(simlod_t* h, uint32_t blocks_per_sm,
 
 SIMLOD_API int simlod_progress(simlod_t* h, uint64_t* finished, uint64_t* submitted) {
   if (!h || !finished) return SIMLOD_ERR_INVALID_ARG;
-  *finished = *reinterpret_cast<volatile uint32_t*>(h->prog_host);
-  if (submitted) *submitted = h->prog_submitted;
+  // the kernel writes the dropped count before its release store of the
+  // finished count: an acquire load of the latter makes the former visible
+  const uint32_t fin = __atomic_load_n(&h->prog_host[0], __ATOMIC_ACQUIRE);
+  const uint32_t dropped = __atomic_load_n(&h->prog_host[1], __ATOMIC_RELAXED);
+  *finished = fin;
+  if (submitted) *submitted = (uint32_t)(h->prog_submitted - dropped);
   return SIMLOD_OK;
 }
 

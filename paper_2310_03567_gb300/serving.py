@@ -15,7 +15,11 @@ When a launch slot is free, the octree with the oldest
 admitted request gets one fused launch (simlod_insert_batches) over its
 admitted requests, each request one batch, in arrival order, up to
 max_points_per_launch points (which bounds how long the requests of other
-octrees wait for a slot). At most
+octrees wait for a slot). The launch gets the time left before the next
+frame as its budget (Section 7.2's frame budget): it stops between requests
+once the frame is due, and the requests it did not reach go back to the head
+of their octree's queue, so that a due frame waits for one request, not for
+the rest of a long launch. At most
 `compute_slots` launches are in flight, and each handle's persistent launch
 uses 1 / compute_slots of every SM, so that the launches in flight always fit
 on the GPU together (their grid barriers wait for all of their blocks). Frames
@@ -167,7 +171,9 @@ class Server:
         self.frame_waits = []
         self.launches = 0
         self.early = 0         # requests completed before the end of their launch
+        self.requeued = 0      # requests a launch's frame budget left for a later launch
         self.gaps = []         # seconds between the starts of consecutive scheduler iterations
+        self.next_frame = None
         self.t0 = None
 
     def reset(self):
@@ -184,7 +190,9 @@ class Server:
         self.busy = [False] * len(self.trees)
         self.launches = 0
         self.early = 0         # requests completed before the end of their launch
+        self.requeued = 0      # requests a launch's frame budget left for a later launch
         self.gaps = []         # seconds between the starts of consecutive scheduler iterations
+        self.next_frame = None
         self.t0 = None
 
     # ------------------------------------------------------------- clock
@@ -204,9 +212,17 @@ class Server:
         for ev, k, reqs, base in self.inflight:
             if ev.query():
                 t = self.now()
-                for r in reqs:
+                applied = len(reqs)
+                if base is not None:
+                    applied = min(applied, (self.trees[k].progress()[0] - base) & 0xFFFFFFFF)
+                for r in reqs[:applied]:
                     if r.done < 0:
                         self._complete(r, t)
+                if applied < len(reqs):
+                    # a budget stop dropped the rest: they go back to the head
+                    # of their octree's queue, in order, with their device copies
+                    self.queued[k] = reqs[applied:] + self.queued[k]
+                    self.requeued += len(reqs) - applied
                 self.busy[k] = False
                 continue
             if base is not None:
@@ -261,8 +277,15 @@ class Server:
             if self.plain:
                 rc = tree.insert(reqs[0].dev, stream=tree.stream, check=False)
             else:
-                base = tree.progress()[1]  # batches handed to this handle's launches so far
-                rc = tree.insert_many_ptrs([r.dev.data_ptr() for r in reqs], [r.n for r in reqs])
+                # nothing of this handle is in flight: its finished count is exact
+                base = tree.progress()[0]
+                budget = None
+                if self.frame_ms and self.next_frame is not None:
+                    # stop between requests once the next frame is due, so that
+                    # the frame waits for one request, not the rest of the launch
+                    budget = max(0, int((self.next_frame - t) * 1e9))
+                rc = tree.insert_many_ptrs([r.dev.data_ptr() for r in reqs], [r.n for r in reqs],
+                                           budget_ns=budget)
             if rc != simlod.OK:
                 raise simlod.SimlodError(rc, "insert")
             ev = torch.cuda.Event()
@@ -310,7 +333,7 @@ class Server:
     def _serve(self, reqs, idle_sleep: float):
         self.t0 = time.perf_counter()
         nxt = 0
-        next_frame = self.frame_ms / 1e3 if self.frame_ms else None
+        self.next_frame = self.frame_ms / 1e3 if self.frame_ms else None
         frame_evs, frame_t, due_t = [], 0.0, None
         t_prev = None
         while nxt < len(reqs) or self.pending or any(self.queued) or self.inflight:
@@ -326,9 +349,10 @@ class Server:
             # a frame that is due holds new launches back until the launches in
             # flight are done, then renders alone: a render's blocks never
             # occupy the SM slots a persistent launch needs on every SM
-            if next_frame is not None and t >= next_frame and due_t is None and not frame_evs:
+            if (self.next_frame is not None and t >= self.next_frame and due_t is None
+                    and not frame_evs):
                 due_t = t
-                next_frame += self.frame_ms / 1e3
+                self.next_frame += self.frame_ms / 1e3
             if due_t is not None and not self.inflight:
                 frame_evs, frame_t = self.render_frame(), self.now()
                 self.frame_waits.append(frame_t - due_t)
@@ -371,6 +395,7 @@ class Server:
                                      "p99": float(np.percentile(gaps, 99)),
                                      "max": float(gaps.max())},
                 "launches": self.launches, "completed_before_launch_end": self.early,
+                "requeued_at_frame": self.requeued,
                 "frames": len(self.frame_times),
                 "frame_ms": {"p50": float(np.percentile(ft, 50)),
                              "p99": float(np.percentile(ft, 99))},

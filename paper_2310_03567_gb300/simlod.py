@@ -136,6 +136,7 @@ SIGNATURES = {
     "simlod_variant_info": (_I32, [_U32, _P]),
     "simlod_compact": (_I32, [_P, _U32, _P]),
     "simlod_progress": (_I32, [_P, ctypes.POINTER(_U64), ctypes.POINTER(_U64)]),
+    "simlod_insert_batches_budget": (_I32, [_P, _P, _P, _U32, _U64, _P]),
 }
 
 
@@ -367,13 +368,18 @@ class Octree:
             raise SimlodError(rc, "simlod_insert_batches")
         return rc
 
-    def insert_many_ptrs(self, ptrs, counts, stream=None) -> int:
-        """Fused form over raw device pointers (no stream ordering done here)."""
+    def insert_many_ptrs(self, ptrs, counts, stream=None, budget_ns: int | None = None) -> int:
+        """Fused form over raw device pointers (no stream ordering done here).
+        With budget_ns, batches after the first start only while the launch
+        has run for at most that long (simlod_insert_batches_budget); the rest
+        are dropped, and progress() tells how many were applied."""
         n = len(ptrs)
         p = (ctypes.c_void_p * max(n, 1))(*ptrs)
         c = (ctypes.c_uint64 * max(n, 1))(*counts)
-        return self._lib.simlod_insert_batches(
-            self._h, p, c, n, _stream_ptr(stream if stream is not None else self.stream))
+        s = _stream_ptr(stream if stream is not None else self.stream)
+        if budget_ns is not None:
+            return self._lib.simlod_insert_batches_budget(self._h, p, c, n, int(budget_ns), s)
+        return self._lib.simlod_insert_batches(self._h, p, c, n, s)
 
     def insert_many_host(self, host_batches, dst, ready, copy_stream, stream=None,
                          check: bool = True) -> int:

@@ -112,6 +112,8 @@ def test_null_handles_are_rejected_before_cuda(lib):
     calls = {
         "simlod_insert_batch_host": (None, None, 0, None),
         "simlod_insert_batches": (None, None, None, 0, None),
+        "simlod_insert_batches_budget": (None, None, None, 0, 0, None),
+        "simlod_progress": (None, None, None),
         "simlod_insert_batches_host": (None, None, None, 0, None, None, None, None),
         "simlod_plan_create": (None, None, None, 0, None, None),
         "simlod_plan_run": (None, None),

@@ -359,7 +359,8 @@ def test_progress_counts_finished_batches():
     finished in host memory. The count rises batch by batch while a launch
     runs and reaches the batches handed over when it ends; a rejected batch
     counts as finished; batches that a frame budget left out are not counted
-    as handed over; plain inserts change neither count."""
+    as handed over (in the blocking and the asynchronous form); plain inserts
+    change neither count."""
     import time
     kw = dict(root_log2=16, leaf_capacity=500, chunk_points=50, grid_log2=6)
     pts = synth.uniform(51, 1 << 16, 300_000)
@@ -386,7 +387,15 @@ def test_progress_counts_finished_batches():
     rest = [simlod.points_tensor(pts[k:k + 10_000]) for k in range(220_000, 260_000, 10_000)]
     rc, used = t.frame_update(rest, budget_ns=0)
     assert rc == simlod.OK and used == 1 and t.progress() == (44, 44)
-    assert t.insert(simlod.points_tensor(pts[230_000:])) == simlod.OK
+    assert t.insert(simlod.points_tensor(pts[230_000:260_000])) == simlod.OK
     assert t.progress() == (44, 44)
-    want = np.concatenate([pts[:200_000], pts[201_000:230_000], pts[230_000:]])
+    # the asynchronous frame budget: one batch, the rest dropped, then passed again
+    more = [simlod.points_tensor(pts[k:k + 10_000]) for k in range(260_000, 300_000, 10_000)]
+    ptrs, cnts = [m.data_ptr() for m in more], [10_000] * 4
+    torch.cuda.synchronize()  # raw pointers: the copies must be done before the launch
+    assert t.insert_many_ptrs(ptrs, cnts, budget_ns=0) == simlod.OK
+    assert t.sync() == simlod.OK and t.progress() == (45, 45)
+    assert t.insert_many_ptrs(ptrs[1:], cnts[1:], budget_ns=10**12) == simlod.OK
+    assert t.sync() == simlod.OK and t.progress() == (48, 48)
+    want = np.concatenate([pts[:200_000], pts[201_000:]])
     assert_snapshots_equal(t.snapshot(), oracle.static_build(ocfg(**kw), want))
