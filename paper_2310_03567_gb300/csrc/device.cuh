@@ -78,6 +78,9 @@ constexpr uint32_t CHUNK_HEADER = 16;
 #ifndef SL_ADVANCE_UNROLL
 #define SL_ADVANCE_UNROLL 1
 #endif
+#ifndef SL_CTL_VIEW
+#define SL_CTL_VIEW 1
+#endif
 #ifndef SL_STORE_PREFETCH
 #define SL_STORE_PREFETCH 1
 #endif

@@ -63,7 +63,19 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // it polls and an arriving block in the value its add returns: every block
 // leaves at its next barrier, and all blocks that run a phase have seen the
 // previous phase complete. Returns false when the launch was aborted.
-__device__ __forceinline__ bool grid_barrier(const Ctx& c, FusedCtl* f) {
+//
+// view != nullptr: thread 0 also reads the control values that the code after
+// this barrier needs (all written before it, none written again before the
+// next one) into the block's shared copy, so that one load per block, not
+// one per warp, reaches the control block's L2 lines.
+struct CtlView {
+  unsigned long long base;
+  uint32_t n_nodes, reject, split_count, ntasks, spill_count, nkeys, stop;
+  int pool_top;
+  uint32_t mv_count[2];
+};
+
+__device__ __forceinline__ bool grid_barrier(const Ctx& c, FusedCtl* f, CtlView* view = nullptr) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -96,6 +108,21 @@ __device__ __forceinline__ bool grid_barrier(const Ctx& c, FusedCtl* f) {
       }
     }
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
+#if SL_CTL_VIEW
+    if (ok && view) {
+      view->base = vload(&c.ctl->base);
+      view->n_nodes = vload(&c.ctl->n_nodes);
+      view->reject = vload(&c.ctl->reject);
+      view->split_count = vload(&c.ctl->split_count);
+      view->ntasks = vload(&c.ctl->ntasks);
+      view->spill_count = vload(&c.ctl->spill_count);
+      view->nkeys = vload(&c.ctl->nkeys);
+      view->pool_top = vload(&c.ctl->pool_top);
+      view->mv_count[0] = vload(&c.ctl->mv_count[0]);
+      view->mv_count[1] = vload(&c.ctl->mv_count[1]);
+      view->stop = vload(&f->stop);
+    }
+#endif
     s_ok = ok;
   }
   __syncthreads();
@@ -176,14 +203,23 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
   const uint32_t nb = n_dev ? min(vload(n_dev), n_batches) : n_batches;
   // the node-table cache is loaded once and patched after every decide round
   node_cache_load(c, smem, 0, vload(&c.ctl->n_nodes));
+#if SL_CTL_VIEW
+  __shared__ CtlView cv;  // control values after the last barrier that filled it
+  CtlView* const vw = &cv;
+#define SL_CV(field, addr) (cv.field)
+#else
+  CtlView* const vw = nullptr;
+#define SL_CV(field, addr) vload(addr)
+#endif
   for (uint32_t b = 0; b < nb; ++b) {
     // every value read here was written before the last barrier and is not
-    // written again before the next one, so all threads decide alike
-    if (vload(&f->stop)) return;
+    // written again before the next one, so all threads decide alike (the
+    // first batch reads them directly: no barrier has filled the view yet)
+    if (b ? SL_CV(stop, &f->stop) : vload(&f->stop)) return;
     if (ready && !wait_ready(c, f, ready + b)) return;
     BatchDesc bd = batches[b];
-    const unsigned long long base = vload(&c.ctl->base);
-    const uint32_t nodes0 = vload(&c.ctl->n_nodes);
+    const unsigned long long base = b ? SL_CV(base, &c.ctl->base) : vload(&c.ctl->base);
+    const uint32_t nodes0 = b ? SL_CV(n_nodes, &c.ctl->n_nodes) : vload(&c.ctl->n_nodes);
     bool rejected = false;
     if (bd.nseg && bd.n) {
       // merged update: gather its batches into the staging buffer
@@ -202,9 +238,9 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
     }
     if (bd.n) {
       phase_count1(c, smem, node_cache_at(smem, nodes0), bd.pts, bd.n, base, warp0, nwarps);
-      if (!grid_barrier(c, f)) return;
+      if (!grid_barrier(c, f, vw)) return;
       clk.tick(c, PH_COUNT);
-      rejected = vload(&c.ctl->reject) != 0u;  // set only by the count round
+      rejected = SL_CV(reject, &c.ctl->reject) != 0u;  // set only by the count round
       if (rejected) {
         phase_rollback(c, nodes0, tid, nthreads);
         if (!grid_barrier(c, f)) return;  // all have read the flag before it is cleared
@@ -221,10 +257,11 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
         for (;;) {
           phase_decide(c, s_lo, s_hi, n_lo, n_hi, iters >= 3 ? (int)((iters - 1) & 1u) : -1,
                        warp0, nwarps);
-          if (!grid_barrier(c, f)) return;
+          if (!grid_barrier(c, f, vw)) return;
           clk.tick(c, PH_DECIDE);
-          const uint32_t sc = vload(&c.ctl->split_count), nn = vload(&c.ctl->n_nodes);
-          const uint32_t nt = vload(&c.ctl->ntasks);
+          const uint32_t sc = SL_CV(split_count, &c.ctl->split_count);
+          const uint32_t nn = SL_CV(n_nodes, &c.ctl->n_nodes);
+          const uint32_t nt = SL_CV(ntasks, &c.ctl->ntasks);
           node_cache_patch(c, smem, s_hi, sc, n_hi, nn);  // this round's splits and new nodes
           if (iters == 1) t_hi = nt;
           else if (nt != t_hi && tid == 0) set_error(c, E_INTERNAL);
@@ -238,17 +275,19 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
           n_lo = n_hi;
           n_hi = nn;
           const int in_list = iters >= 2 ? (int)((iters - 2) & 1u) : -1;
-          const uint32_t n_in = in_list >= 0 ? vload(&c.ctl->mv_count[in_list]) : 0u;
+          const uint32_t n_in =
+              in_list >= 0 ? SL_CV(mv_count[in_list], &c.ctl->mv_count[in_list]) : 0u;
           phase_advance(c, smem, node_cache_at(smem, nn), bd.pts, bd.n, base, t_hi, s_lo, s_hi,
                         in_list, n_in, (int)((iters - 1) & 1u), warp0, nwarps);
           ++iters;
           if (!grid_barrier(c, f)) return;
           clk.tick(c, PH_ADVANCE);
         }
-        const uint32_t n_tasks = vload(&c.ctl->ntasks);
-        const uint32_t n_spill = min(vload(&c.ctl->spill_count), c.spill_cap);
-        const uint32_t n_keys = min(vload(&c.ctl->nkeys), c.backlog_cap);
-        const int pool_top = vload(&c.ctl->pool_top);
+        // (the last decide round's barrier filled the view)
+        const uint32_t n_tasks = SL_CV(ntasks, &c.ctl->ntasks);
+        const uint32_t n_spill = min(SL_CV(spill_count, &c.ctl->spill_count), c.spill_cap);
+        const uint32_t n_keys = min(SL_CV(nkeys, &c.ctl->nkeys), c.backlog_cap);
+        const int pool_top = SL_CV(pool_top, &c.ctl->pool_top);
         phase_store(c, smem, bd.pts, bd.n, base, n_spill, n_tasks, n_keys, pool_top, tid,
                     nthreads);
         if (!grid_barrier(c, f)) return;
@@ -281,11 +320,12 @@ __global__ void __launch_bounds__(FUSED_BLOCK, PHASE_MIN_BLOCKS) k_fused(Ctx c, 
                      : "memory");
       }
     }
-    if (!grid_barrier(c, f)) return;
+    if (!grid_barrier(c, f, vw)) return;  // the next batch reads stop, base and n_nodes
     clk.tick(c, PH_END);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0)
     atomicAdd(&c.ctl->phase_ns[PH_LAUNCH], globaltimer_ns() - t_begin);
+#undef SL_CV
 }
 
 // ------------------------------------------------------------ batched form
