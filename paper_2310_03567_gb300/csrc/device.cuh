@@ -81,6 +81,9 @@ constexpr uint32_t CHUNK_HEADER = 16;
 #ifndef SL_CTL_VIEW
 #define SL_CTL_VIEW 1
 #endif
+#ifndef SL_CTL_SPREAD
+#define SL_CTL_SPREAD 1
+#endif
 #ifndef SL_STORE_PREFETCH
 #define SL_STORE_PREFETCH 1
 #endif
@@ -145,26 +148,34 @@ enum : uint32_t {
 };
 
 // Control block at the start of the arena.
+// The counters that warps all over the grid change with atomics inside a
+// phase (SL_HOT) each start a 128-byte line of their own, so that their
+// atomics spread over several L2 slices instead of queueing at one.
+#if SL_CTL_SPREAD
+#define SL_HOT alignas(128)
+#else
+#define SL_HOT
+#endif
 struct Ctl {
-  unsigned long long base;           // gidx of the next accepted point
-  unsigned long long bump;           // bytes taken from the data region
-  unsigned long long chunks_bumped;  // chunks taken from the data region
-  unsigned int n_nodes;
-  int pool_top;                      // chunk refs in the pool
-  unsigned int error;                // sticky E_* bits
-  unsigned int reject;               // out-of-cube point seen in this update
-  unsigned int spill_count;          // re-inserted points of this update
-  unsigned int nkeys;                // new voxels (backlog entries) of this update
-  unsigned int alloc_seq;            // alloc_refs entries of this update
-  unsigned int split_count;          // split-list entries of this update
-  unsigned int ntasks;               // spill tasks (= freed chunks) of this update
-  unsigned int vis_count;            // nodes drawn by the last render
+  unsigned long long base;                  // gidx of the next accepted point
+  SL_HOT unsigned long long bump;           // bytes taken from the data region
+  unsigned long long chunks_bumped;         // chunks taken from the data region
+  SL_HOT unsigned int n_nodes;
+  SL_HOT int pool_top;                      // chunk refs in the pool
+  unsigned int error;                       // sticky E_* bits
+  unsigned int reject;                      // out-of-cube point seen in this update
+  SL_HOT unsigned int spill_count;          // re-inserted points of this update
+  SL_HOT unsigned int nkeys;                // new voxels (backlog entries) of this update
+  SL_HOT unsigned int alloc_seq;            // alloc_refs entries of this update
+  SL_HOT unsigned int split_count;          // split-list entries of this update
+  SL_HOT unsigned int ntasks;               // spill tasks (= freed chunks) of this update
+  unsigned int vis_count;                   // nodes drawn by the last render
   unsigned long long st_batches, st_points, st_rejected, st_spilled, st_splits, st_voxels,
       st_iter_max, st_rounds;
   unsigned long long last_points, last_spilled, last_splits, last_voxels, last_iters;
   unsigned long long st_rejected_async;  // rejections inside fused launches
-  unsigned int mv_count[2];              // entries of the two mover lists
-  unsigned long long render_samples;     // points and voxels visited by the last render
+  SL_HOT unsigned int mv_count[2];       // entries of the two mover lists
+  SL_HOT unsigned long long render_samples;  // points and voxels visited by the last render
   unsigned long long phase_ns[8];        // fused form: time per phase (see PH_*)
   unsigned long long st_compacted;       // nodes turned into arrays (simlod_compact), in all
   unsigned long long st_compact_chunks;  // chunks those nodes gave back to the pool
@@ -173,6 +184,7 @@ struct Ctl {
   unsigned long long compact_chunks_now; // chunks those arrays stand in for
   unsigned long long pad_ctl;
 };
+#undef SL_HOT
 static_assert(sizeof(Ctl) % 16 == 0, "Ctl size");
 
 // Phases of the fused form, for its phase clock.
