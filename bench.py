@@ -59,9 +59,9 @@ def update_alg_bytes(B, S, V, K, grid_bytes):
 KERNEL_SOURCES = ("paper_2310_03567_gb300/csrc/device.cuh", "paper_2310_03567_gb300/csrc/fused.cuh",
                   "include/simlod.h", "paper_2310_03567_gb300/_build.py")
 TRAFFIC_PER_LAUNCH = {
-    # clustered-300M, one launch over its 54 batches: 38.98 GB read + 23.29 GB
-    # written in 52.50 ms (profiles/k_fused_clustered300m_dram.md)
-    ("ecb69f0c1ba8a779", "clustered-300000000"): 62.27e9,
+    # clustered-300M, one launch over its 54 batches: 38.97 GB read + 23.28 GB
+    # written in 50.94 ms (profiles/k_fused_clustered300m_dram.md)
+    ("c52008331cfebe98", "clustered-300000000"): 62.25e9,
 }
 
 

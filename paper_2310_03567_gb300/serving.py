@@ -25,10 +25,11 @@ uses 1 / compute_slots of every SM, so that the launches in flight always fit
 on the GPU together (their grid barriers wait for all of their blocks). Frames
 are enqueued on each octree's stream after the updates before them, so a
 frame shows every request completed before it and none half-applied. A frame
-that is due holds new launches back until the launches in flight have
-finished and renders alone: render blocks that took SM slots beside one
-persistent launch would hold back the next persistent launch, which needs a
-slot on every SM.
+that is due holds new launches back until every octree has rendered; an
+octree renders as soon as no launch of its own is in flight, beside launches
+of other octrees that are still running: render blocks that took SM slots
+while a persistent launch waits to start would hold it back, since it needs
+a slot on every SM, but no launch starts before the frame is done.
 
 A request of the serving form completes when its own batch of the launch is
 finished (the library's progress count, which the persistent kernel writes
@@ -294,23 +295,24 @@ class Server:
             self.busy[k] = True
             self.launches += 1
 
+    def render_one(self, k: int):
+        """Render octree k into its own frame on its stream; returns the
+        render's completion event."""
+        torch = self.torch
+        tree = self.trees[k]
+        if self.frames[k] is None:
+            with torch.cuda.stream(tree.stream):
+                self.frames[k] = torch.empty((FRAME_H, FRAME_W), dtype=torch.int64,
+                                             device="cuda")
+        tree.render(self.cams[k], self.frames[k])
+        ev = torch.cuda.Event()
+        ev.record(tree.stream)
+        return ev
+
     def render_frame(self):
         """Render every octree into its own frame on its stream; returns the
         frame's completion events."""
-        torch = self.torch
-        evs = []
-        for k, tree in enumerate(self.trees):
-            if self.cams[k] is None:
-                continue
-            if self.frames[k] is None:
-                with torch.cuda.stream(tree.stream):
-                    self.frames[k] = torch.empty((FRAME_H, FRAME_W), dtype=torch.int64,
-                                                 device="cuda")
-            tree.render(self.cams[k], self.frames[k])
-            ev = torch.cuda.Event()
-            ev.record(tree.stream)
-            evs.append(ev)
-        return evs
+        return [self.render_one(k) for k in range(len(self.trees)) if self.cams[k] is not None]
 
     # --------------------------------------------------------------- run
     def run(self, requests, idle_sleep: float = 5e-5):
@@ -334,7 +336,7 @@ class Server:
         self.t0 = time.perf_counter()
         nxt = 0
         self.next_frame = self.frame_ms / 1e3 if self.frame_ms else None
-        frame_evs, frame_t, due_t = [], 0.0, None
+        frame_evs, frame_t, due_t, todo = [], 0.0, None, []
         t_prev = None
         while nxt < len(reqs) or self.pending or any(self.queued) or self.inflight:
             t = self.now()
@@ -346,20 +348,32 @@ class Server:
                 nxt += 1
             self._poll()
             self._admit()
-            # a frame that is due holds new launches back until the launches in
-            # flight are done, then renders alone: a render's blocks never
-            # occupy the SM slots a persistent launch needs on every SM
+            # a frame that is due holds new launches back until every octree
+            # has rendered: an octree renders as soon as no launch of its own is
+            # in flight, beside the launches of other octrees that are still
+            # running (all their blocks are resident); a render's blocks never
+            # occupy SM slots that a persistent launch still waits for, since
+            # none starts before the frame is done
             if (self.next_frame is not None and t >= self.next_frame and due_t is None
                     and not frame_evs):
                 due_t = t
                 self.next_frame += self.frame_ms / 1e3
-            if due_t is not None and not self.inflight:
-                frame_evs, frame_t = self.render_frame(), self.now()
-                self.frame_waits.append(frame_t - due_t)
-                due_t = None
+                todo = [k for k in range(len(self.trees)) if self.cams[k] is not None]
+            if due_t is not None:
+                left = []
+                for k in todo:
+                    if self.busy[k]:
+                        left.append(k)
+                    else:
+                        frame_evs.append(self.render_one(k))
+                todo = left
+                if not todo:
+                    frame_t = self.now()
+                    self.frame_waits.append(frame_t - due_t)
+                    due_t = None
             if due_t is None and not frame_evs:
                 self._launch()
-            if frame_evs and all(e.query() for e in frame_evs):
+            if due_t is None and frame_evs and all(e.query() for e in frame_evs):
                 self.frame_times.append(self.now() - frame_t)
                 frame_evs = []
             time.sleep(idle_sleep)
