@@ -789,9 +789,10 @@ def serving_form(args, rank: int = 0) -> dict:
     """Serving form: requests (log-uniform 100k-5M points) arrive by a Poisson
     process at ~70 % of the plain path's measured capacity; the same traces
     are served by the serving form and by a plain server (one request per
-    update, one update at a time). Latency percentiles pool the requests of
-    the measured traces (after one untimed warm-up trace); a saturated run
-    queues a whole trace at once."""
+    update, one update at a time), taking turns trace by trace; each server
+    serves its trace once untimed, then timed. Latency percentiles pool the
+    requests of the timed traces; a saturated run queues a whole trace at
+    once."""
     import torch
 
     from paper_2310_03567_gb300 import serving, simlod
@@ -820,29 +821,34 @@ def serving_form(args, rank: int = 0) -> dict:
     out = {}
     clk = None
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
-    for name, plain in (("serving", False), ("plain", True)):
-        lat, wait, reps = [], [], []
-        srv = serving.Server(specs, hbm_budget=budget, compute_slots=2, frame_ms=33.3,
-                             plain=plain)
-        # an untimed warm-up run of the first trace, then the measured traces,
-        # all on the same resident octrees (reset between traces)
-        for t, tr in enumerate([traces[0]] + traces):
-            for r in tr:
-                r.admitted = r.launched = r.done = -1.0
-            srv.reset()
-            if not plain and t == 1:
-                clocks.start()
-            done = srv.run(tr)
-            if not plain and t == 1:
-                clk = clocks.stop()
-            if t == 0:
-                continue
+    # the two servers take turns, one trace each, the first of each turn
+    # alternating, so that a box that drifts during the run (some get slower
+    # over minutes) weighs on both alike; every server is built for its trace
+    # and serves it once untimed first (the first run after a build is slower)
+    meas = {"serving": ([], [], []), "plain": ([], [], [])}
+    for t, tr in enumerate(traces):
+        order = (("serving", False), ("plain", True))
+        for name, plain in (order if t % 2 == 0 else order[::-1]):
+            lat, wait, reps = meas[name]
+            srv = serving.Server(specs, hbm_budget=budget, compute_slots=2, frame_ms=33.3,
+                                 plain=plain)
+            for warm in (True, False):
+                for r in tr:
+                    r.admitted = r.launched = r.done = -1.0
+                srv.reset()
+                if not warm and not plain and t == 0:
+                    clocks.start()
+                done = srv.run(tr)
+                if not warm and not plain and t == 0:
+                    clk = clocks.stop()
             lat += [(r.done - r.arrival) * 1e3 for r in done]
             wait += [(r.admitted - r.arrival) * 1e3 for r in done]
             reps.append(srv.report())
-        srv.close()
-        del srv
-        torch.cuda.empty_cache()
+            srv.close()
+            del srv
+            torch.cuda.empty_cache()
+    for name in ("serving", "plain"):
+        lat, wait, reps = meas[name]
         rep = dict(reps[0])
         rep["traces"] = len(traces)
         rep["requests"] = len(lat)
