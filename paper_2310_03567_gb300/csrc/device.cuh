@@ -491,8 +491,15 @@ __device__ __forceinline__ ulonglong2 slot_load(const HSlot* s) {
 // runs of 2^SL_HASH_BUCKET cells along x share one randomly placed bucket of
 // slots, so the neighbouring cells that a warp claims fall on a few cache
 // lines; otherwise every key is placed at random.
+#ifndef SL_HASH_FIB
+#define SL_HASH_FIB 0
+#endif
 __device__ __forceinline__ uint32_t claim_slot(const Ctx& c, unsigned long long key) {
-#if SL_HASH_BUCKET
+#if SL_HASH_FIB
+  // multiplicative hashing: the top log2(slots) bits of key * 2^64 / phi
+  const uint32_t bits = (uint32_t)__popc(c.hash_mask);
+  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64u - bits)) & c.hash_mask;
+#elif SL_HASH_BUCKET
   constexpr uint32_t B = SL_HASH_BUCKET;
   return (((uint32_t)fmix64(key >> B) << B) | ((uint32_t)key & ((1u << B) - 1u))) & c.hash_mask;
 #else

@@ -24,12 +24,16 @@ the rest of a long launch. At most
 uses 1 / compute_slots of every SM, so that the launches in flight always fit
 on the GPU together (their grid barriers wait for all of their blocks). Frames
 are enqueued on each octree's stream after the updates before them, so a
-frame shows every request completed before it and none half-applied. A frame
-that is due holds new launches back until every octree has rendered; an
-octree renders as soon as no launch of its own is in flight, beside launches
-of other octrees that are still running: render blocks that took SM slots
-while a persistent launch waits to start would hold it back, since it needs
-a slot on every SM, but no launch starts before the frame is done.
+frame shows every request completed before it and none half-applied. When a
+frame is due, every octree renders as soon as no launch of its own is in
+flight (the launches in flight stop at their frame budget), beside the
+launches of other octrees that are still running. Meanwhile the octrees that
+have rendered keep being served, on the slots that neither a launch in
+flight nor the render of an octree whose launch was in flight at the due
+time needs: a persistent launch that starts beside the frame's render blocks
+finds its last SM slots once those short blocks have finished, and nothing
+waits on a launch, so nothing waits for ever (serve_during_frame=False holds
+every new launch back until the frame is done instead).
 
 A request of the serving form completes when its own batch of the launch is
 finished (the library's progress count, which the persistent kernel writes
@@ -124,16 +128,20 @@ class StagingPool:
 class Server:
     def __init__(self, specs, hbm_budget: int, compute_slots: int = 2, frame_ms: float = 0.0,
                  max_batches_per_launch: int = 64, max_points_per_launch: int = 8_000_000,
-                 plain: bool = False, staging_cap: int = 8 << 30):
+                 plain: bool = False, staging_cap: int = 8 << 30,
+                 serve_during_frame: bool = True):
         """plain=True serves with the plain per-kernel path instead: one
         request per update, one update at a time (the baseline). The budget
         left by the arenas, at most staging_cap bytes, is the staging buffer
-        of the requests in flight."""
+        of the requests in flight. serve_during_frame=False holds every new
+        launch back from the moment a frame is due until it has been
+        rendered."""
         import torch
         self.torch = torch
         if compute_slots < 1:
             raise ValueError("compute_slots must be at least 1")
         self.plain = plain
+        self.serve_during_frame = serve_during_frame
         if plain:
             compute_slots, max_batches_per_launch = 1, 1
         self.budget = int(hbm_budget)
@@ -257,10 +265,14 @@ class Server:
             r.admitted = self.now()
             self.queued[r.octree].append(r)
 
-    def _launch(self):
+    def _launch(self, limit=None, exclude=()):
+        """Start launches while fewer than `limit` (default: every slot) are
+        in flight; octrees in `exclude` wait."""
         torch = self.torch
-        while len(self.inflight) < self.slots:
-            ready = [k for k in range(len(self.trees)) if self.queued[k] and not self.busy[k]]
+        limit = self.slots if limit is None else limit
+        while len(self.inflight) < limit:
+            ready = [k for k in range(len(self.trees))
+                     if self.queued[k] and not self.busy[k] and k not in exclude]
             if not ready:
                 return
             k = min(ready, key=lambda j: self.queued[j][0].arrival)
@@ -337,6 +349,7 @@ class Server:
         nxt = 0
         self.next_frame = self.frame_ms / 1e3 if self.frame_ms else None
         frame_evs, frame_t, due_t, todo = [], 0.0, None, []
+        busy_at_due, held = set(), []
         t_prev = None
         while nxt < len(reqs) or self.pending or any(self.queued) or self.inflight:
             t = self.now()
@@ -348,24 +361,26 @@ class Server:
                 nxt += 1
             self._poll()
             self._admit()
-            # a frame that is due holds new launches back until every octree
-            # has rendered: an octree renders as soon as no launch of its own is
-            # in flight, beside the launches of other octrees that are still
-            # running (all their blocks are resident); a render's blocks never
-            # occupy SM slots that a persistent launch still waits for, since
-            # none starts before the frame is done
+            # a frame that is due: every octree renders as soon as no launch
+            # of its own is in flight (the launches in flight stop at their
+            # frame budget), beside the launches of other octrees that are
+            # still running (all their blocks are resident)
             if (self.next_frame is not None and t >= self.next_frame and due_t is None
                     and not frame_evs):
                 due_t = t
                 self.next_frame += self.frame_ms / 1e3
                 todo = [k for k in range(len(self.trees)) if self.cams[k] is not None]
+                busy_at_due = {k for k in todo if self.busy[k]}
             if due_t is not None:
                 left = []
                 for k in todo:
                     if self.busy[k]:
                         left.append(k)
                     else:
-                        frame_evs.append(self.render_one(k))
+                        ev = self.render_one(k)
+                        frame_evs.append(ev)
+                        if k in busy_at_due:
+                            held.append(ev)
                 todo = left
                 if not todo:
                     frame_t = self.now()
@@ -373,9 +388,20 @@ class Server:
                     due_t = None
             if due_t is None and not frame_evs:
                 self._launch()
+            elif self.serve_during_frame:
+                # while the frame is pending, octrees that have rendered keep
+                # being served on the slots that no launch in flight and no
+                # render of an octree whose launch was in flight at the due
+                # time needs: such a render takes the SM slots its launch
+                # left, and a new persistent launch (which needs a block on
+                # every SM) only finds its slots once the short render blocks
+                # beside it have finished; nothing waits on a launch, so
+                # nothing can wait for ever
+                held = [e for e in held if not e.query()]
+                self._launch(limit=self.slots - len(held), exclude=set(todo))
             if due_t is None and frame_evs and all(e.query() for e in frame_evs):
                 self.frame_times.append(self.now() - frame_t)
-                frame_evs = []
+                frame_evs, held = [], []
             time.sleep(idle_sleep)
         for e in frame_evs:
             e.synchronize()
