@@ -65,6 +65,42 @@ TRAFFIC_PER_LAUNCH = {
 }
 
 
+def paper_style_roofline(B, S, V, K, grid_bytes, peak_gbs, mpts):
+    """The same roofline with the paper's 16-byte records only (no 4-byte
+    gidx stored beside each point): 16 B read + 16 B written per point, 32 B
+    per re-inserted point."""
+    b = 16 * B + 16 * B + 32 * S + 16 * V + grid_bytes * K
+    roof = B / (b / (peak_gbs * 1e9)) / 1e6
+    return {"alg_bytes_per_point": b / B, "roofline_mpts": roof, "frac": mpts / roof}
+
+
+def host_cpu() -> dict:
+    """The host's CPU model and core count (for the CPU oracle's numbers)."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model name"):
+                    model = v.strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                k, _, v = line.partition(":")
+                if k.strip() == "Model name":
+                    model = v.strip()
+                    break
+        except Exception:
+            pass
+    return {"model": model or platform.processor() or "unknown", "arch": platform.machine(),
+            "nproc": os.cpu_count()}
+
+
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
@@ -171,7 +207,7 @@ def cpu_baseline(workload, budget_s: float = 12.0):
     inc.close()
     return {"value": pts / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {nb} batches ({pts} points) of {w.name}, sequential incremental "
-                      f"oracle, {dt:.1f} s"}
+                      f"oracle, {dt:.1f} s", "host": host_cpu()}
 
 
 def workload_config(w, max_batch: int, world: int) -> dict:
@@ -228,7 +264,7 @@ def run_reference(args):
             "config": workload_config(w, max(int(c) for c in w.counts), world),
             "sample": {"batches_per_step": nb, "points_per_step": pts},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": what},
+                             "sample": what, "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -600,7 +636,9 @@ def run_ours(args):
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "alg_bytes_per_launch": upd_bytes, "peak_source": peak_src},
         "update_roofline": {"alg_bytes_per_point": upd_bytes / B, "roofline_mpts": roofline_mpts,
-                            "frac": value / world / roofline_mpts},
+                            "frac": value / world / roofline_mpts,
+                            "paper_style": paper_style_roofline(B, S, V, K, grid_bytes,
+                                                                peak, value / world)},
         "update_counts": {"B": B, "S": S, "V": V, "K": K, "rounds": stats["rounds"],
                           "nodes": stats["nodes"]},
         "fused_phase_ms_per_step": phases,

@@ -487,17 +487,19 @@ __device__ __forceinline__ ulonglong2 slot_load(const HSlot* s) {
   return kv;
 }
 
-// First claim-table slot of a key (node << 3G | cell). With SL_HASH_BUCKET,
-// runs of 2^SL_HASH_BUCKET cells along x share one randomly placed bucket of
-// slots, so the neighbouring cells that a warp claims fall on a few cache
-// lines; otherwise every key is placed at random.
+// First claim-table slot of a key (node << 3G | cell). By default it is the
+// top log2(slots) bits of key * 2^64 / phi (multiplicative hashing: one
+// 64-bit multiply instead of the two of a 64-bit finalizer; where a key sits
+// does not change which point wins). With SL_HASH_FIB=0 a 64-bit finalizer
+// places every key at random, or, with SL_HASH_BUCKET, runs of
+// 2^SL_HASH_BUCKET cells along x share one randomly placed bucket of slots,
+// so that the neighbouring cells a warp claims fall on a few cache lines.
 #ifndef SL_HASH_FIB
-#define SL_HASH_FIB 0
+#define SL_HASH_FIB 1
 #endif
 __device__ __forceinline__ uint32_t claim_slot(const Ctx& c, unsigned long long key) {
 #if SL_HASH_FIB
-  // multiplicative hashing: the top log2(slots) bits of key * 2^64 / phi
-  const uint32_t bits = (uint32_t)__popc(c.hash_mask);
+  const uint32_t bits = (uint32_t)__popc(c.hash_mask);  // the table has at least 2 slots
   return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64u - bits)) & c.hash_mask;
 #elif SL_HASH_BUCKET
   constexpr uint32_t B = SL_HASH_BUCKET;
