@@ -59,9 +59,9 @@ def update_alg_bytes(B, S, V, K, grid_bytes):
 KERNEL_SOURCES = ("paper_2310_03567_gb300/csrc/device.cuh", "paper_2310_03567_gb300/csrc/fused.cuh",
                   "include/simlod.h", "paper_2310_03567_gb300/_build.py")
 TRAFFIC_PER_LAUNCH = {
-    # clustered-300M, one launch over its 54 batches: 38.97 GB read + 23.28 GB
-    # written in 50.94 ms (profiles/k_fused_clustered300m_dram.md)
-    ("c52008331cfebe98", "clustered-300000000"): 62.25e9,
+    # clustered-300M, one launch over its 54 batches: 39.02 GB read + 23.28 GB
+    # written in 49.81 ms (profiles/k_fused_clustered300m_dram.md)
+    ("b139f6fe313e84b4", "clustered-300000000"): 62.31e9,
 }
 
 
@@ -875,11 +875,11 @@ def serving_form(args, rank: int = 0) -> dict:
     # alternating, so that a box that drifts during the run (some get slower
     # over minutes) weighs on both alike; every server is built for its trace
     # and serves it once untimed first (the first run after a build is slower)
-    meas = {"serving": ([], [], []), "plain": ([], [], [])}
+    meas = {"serving": ([], [], [], [], [], []), "plain": ([], [], [], [], [], [])}
     for t, tr in enumerate(traces):
         order = (("serving", False), ("plain", True))
         for name, plain in (order if t % 2 == 0 else order[::-1]):
-            lat, wait, reps = meas[name]
+            lat, wait, reps, lwait, serv, slow = meas[name]
             srv = serving.Server(specs, hbm_budget=budget, compute_slots=2, frame_ms=33.3,
                                  plain=plain)
             for warm in (True, False):
@@ -893,13 +893,23 @@ def serving_form(args, rank: int = 0) -> dict:
                     clk = clocks.stop()
             lat += [(r.done - r.arrival) * 1e3 for r in done]
             wait += [(r.admitted - r.arrival) * 1e3 for r in done]
+            lwait += [(r.launched - r.admitted) * 1e3 for r in done]
+            serv += [(r.done - r.launched) * 1e3 for r in done]
             reps.append(srv.report())
+            slow += [dict(x, trace=t) for x in reps[-1]["slowest"]]
             srv.close()
             del srv
             torch.cuda.empty_cache()
     for name in ("serving", "plain"):
-        lat, wait, reps = meas[name]
+        lat, wait, reps, lwait, serv, slow = meas[name]
         rep = dict(reps[0])
+        # frames and scheduler figures are the first trace's; latencies,
+        # waits and service times pool every timed trace's requests
+        rep["launch_wait_ms"] = {"p50": float(np.percentile(lwait, 50)),
+                                 "p99": float(np.percentile(lwait, 99))}
+        rep["service_ms"] = {"p50": float(np.percentile(serv, 50)),
+                             "p99": float(np.percentile(serv, 99))}
+        rep["slowest"] = sorted(slow, key=lambda x: -x["latency_ms"])[:8]
         rep["traces"] = len(traces)
         rep["requests"] = len(lat)
         rep["mpts_per_s"] = float(np.mean([x["mpts_per_s"] for x in reps]))
@@ -1035,7 +1045,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="clustered",
                     choices=["aerial", "uniform", "clustered", "mixed", "serving"])
-    ap.add_argument("--serving-traces", type=int, default=3,
+    ap.add_argument("--serving-traces", type=int, default=5,
                     help="independent Poisson traces whose requests the serving latency pools")
     ap.add_argument("--serving-scale", type=float, default=1.0,
                     help="octree sizes of the serving workload relative to 5M-200M points")

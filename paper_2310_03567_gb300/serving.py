@@ -32,7 +32,7 @@ have rendered keep being served, on the slots that neither a launch in
 flight nor the render of an octree whose launch was in flight at the due
 time needs: a persistent launch that starts beside the frame's render blocks
 finds its last SM slots once those short blocks have finished, and nothing
-waits on a launch, so nothing waits for ever (serve_during_frame=False holds
+waits on a launch, so nothing waits for ever (frame_policy="hold" holds
 every new launch back until the frame is done instead).
 
 A request of the serving form completes when its own batch of the launch is
@@ -129,19 +129,23 @@ class Server:
     def __init__(self, specs, hbm_budget: int, compute_slots: int = 2, frame_ms: float = 0.0,
                  max_batches_per_launch: int = 64, max_points_per_launch: int = 8_000_000,
                  plain: bool = False, staging_cap: int = 8 << 30,
-                 serve_during_frame: bool = True):
+                 frame_policy: str = "held"):
         """plain=True serves with the plain per-kernel path instead: one
         request per update, one update at a time (the baseline). The budget
         left by the arenas, at most staging_cap bytes, is the staging buffer
-        of the requests in flight. serve_during_frame=False holds every new
-        launch back from the moment a frame is due until it has been
-        rendered."""
+        of the requests in flight. frame_policy "held" keeps serving the
+        octrees that have rendered while a frame is pending, on the slots
+        that the renders of octrees busy at the due time do not hold; "hold"
+        holds every new launch back from the moment a frame is due until it
+        has been rendered."""
         import torch
         self.torch = torch
         if compute_slots < 1:
             raise ValueError("compute_slots must be at least 1")
         self.plain = plain
-        self.serve_during_frame = serve_during_frame
+        if frame_policy not in ("held", "hold"):
+            raise ValueError(f"unknown frame policy {frame_policy!r}")
+        self.frame_policy = frame_policy
         if plain:
             compute_slots, max_batches_per_launch = 1, 1
         self.budget = int(hbm_budget)
@@ -178,6 +182,7 @@ class Server:
         self.finished = []
         self.frame_times = []
         self.frame_waits = []
+        self.frame_spans = []  # (due, rendered) per frame, server clock
         self.launches = 0
         self.early = 0         # requests completed before the end of their launch
         self.requeued = 0      # requests a launch's frame budget left for a later launch
@@ -196,6 +201,7 @@ class Server:
                 raise simlod.SimlodError(tree.sync(), "reset")
         self.pool = StagingPool(self.pool.size)
         self.finished, self.frame_times, self.frame_waits = [], [], []
+        self.frame_spans = []
         self.busy = [False] * len(self.trees)
         self.launches = 0
         self.early = 0         # requests completed before the end of their launch
@@ -348,7 +354,7 @@ class Server:
         self.t0 = time.perf_counter()
         nxt = 0
         self.next_frame = self.frame_ms / 1e3 if self.frame_ms else None
-        frame_evs, frame_t, due_t, todo = [], 0.0, None, []
+        frame_evs, frame_t, due_t, todo, frame_due = [], 0.0, None, [], 0.0
         busy_at_due, held = set(), []
         t_prev = None
         while nxt < len(reqs) or self.pending or any(self.queued) or self.inflight:
@@ -385,12 +391,13 @@ class Server:
                 if not todo:
                     frame_t = self.now()
                     self.frame_waits.append(frame_t - due_t)
+                    frame_due = due_t
                     due_t = None
             if due_t is None and not frame_evs:
                 self._launch()
-            elif self.serve_during_frame:
+            elif self.frame_policy == "held":
                 # while the frame is pending, octrees that have rendered keep
-                # being served on the slots that no launch in flight and no
+                # being served, on the slots that no launch in flight and no
                 # render of an octree whose launch was in flight at the due
                 # time needs: such a render takes the SM slots its launch
                 # left, and a new persistent launch (which needs a block on
@@ -401,6 +408,7 @@ class Server:
                 self._launch(limit=self.slots - len(held), exclude=set(todo))
             if due_t is None and frame_evs and all(e.query() for e in frame_evs):
                 self.frame_times.append(self.now() - frame_t)
+                self.frame_spans.append((frame_due, self.now()))
                 frame_evs, held = [], []
             time.sleep(idle_sleep)
         for e in frame_evs:
@@ -421,6 +429,18 @@ class Server:
         queue = np.array([r.launched - r.admitted for r in self.finished]) * 1e3
         service = np.array([r.done - r.launched for r in self.finished]) * 1e3
         gaps = np.array(self.gaps) * 1e3 if self.gaps else np.zeros(1)
+        # anatomy of the tail: the slowest requests, their waits and service,
+        # the launch that applied them, and how long a frame was pending
+        # while they were in flight
+        slow = []
+        for r in sorted(self.finished, key=lambda r: r.arrival - r.done)[:8]:
+            pend = sum(max(0.0, min(r.done, b) - max(r.arrival, a)) for a, b in self.frame_spans)
+            slow.append({"octree": r.octree, "points": r.n,
+                         "latency_ms": (r.done - r.arrival) * 1e3,
+                         "admission_wait_ms": (r.admitted - r.arrival) * 1e3,
+                         "launch_wait_ms": (r.launched - r.admitted) * 1e3,
+                         "service_ms": (r.done - r.launched) * 1e3,
+                         "launch_points": r.launch_points, "frame_pending_ms": pend * 1e3})
         return {"requests": len(self.finished), "points": pts, "seconds": span,
                 "mpts_per_s": pts / span / 1e6 if span > 0 else 0.0,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)),
@@ -440,7 +460,8 @@ class Server:
                 "frame_ms": {"p50": float(np.percentile(ft, 50)),
                              "p99": float(np.percentile(ft, 99))},
                 "frame_wait_ms": {"p50": float(np.percentile(fw, 50)),
-                                  "p99": float(np.percentile(fw, 99))}}
+                                  "p99": float(np.percentile(fw, 99))},
+                "slowest": slow}
 
     def close(self):
         for t in self.trees:
