@@ -81,3 +81,37 @@ def test_staging_pool_random_use_never_overlaps():
     for off, n in list(live.items()):
         pool.release(off, n)
     assert pool.free == [(0, pool.size)]
+
+
+def _finished(rows):
+    """Requests with given (octree, arrival, admitted, launched, done) times."""
+    out = []
+    for k, a, ad, la, d in rows:
+        r = serving.Request(octree=k, points=np.zeros((1000, 4), np.int32), arrival=a)
+        r.admitted, r.launched, r.done, r.launch_points = ad, la, d, 1000
+        out.append(r)
+    return out
+
+
+def test_report_lists_the_slowest_requests_with_their_anatomy():
+    srv = serving.Server.__new__(serving.Server)  # the report needs no device
+    srv.finished = _finished([(0, 0.000, 0.0001, 0.0002, 0.0010),
+                              (1, 0.001, 0.0011, 0.0060, 0.0090),   # slowest: 8 ms
+                              (2, 0.002, 0.0021, 0.0022, 0.0050)])
+    srv.frame_spans = [(0.004, 0.007)]  # a frame pending from 4 to 7 ms
+    srv.frame_times, srv.frame_waits, srv.gaps = [0.002], [0.001], [1e-4]
+    srv.launches, srv.early, srv.requeued = 3, 0, 0
+    rep = srv.report()
+    first, second = rep["slowest"][:2]
+    assert first["octree"] == 1 and abs(first["latency_ms"] - 8.0) < 1e-9
+    assert abs(first["launch_wait_ms"] - 4.9) < 1e-9 and abs(first["service_ms"] - 3.0) < 1e-9
+    assert abs(first["admission_wait_ms"] - 0.1) < 1e-9
+    assert abs(first["frame_pending_ms"] - 3.0) < 1e-9   # the whole frame lies inside it
+    assert second["octree"] == 2 and abs(second["frame_pending_ms"] - 1.0) < 1e-9  # 4 to 5 ms
+    assert rep["slowest"][2]["frame_pending_ms"] == 0.0
+
+
+def test_unknown_frame_policy_is_refused():
+    import pytest
+    with pytest.raises(ValueError):
+        serving.Server([], hbm_budget=0, frame_policy="sometimes")
