@@ -59,9 +59,9 @@ def update_alg_bytes(B, S, V, K, grid_bytes):
 KERNEL_SOURCES = ("paper_2310_03567_gb300/csrc/device.cuh", "paper_2310_03567_gb300/csrc/fused.cuh",
                   "include/simlod.h", "paper_2310_03567_gb300/_build.py")
 TRAFFIC_PER_LAUNCH = {
-    # clustered-300M, one launch over its 54 batches: 39.02 GB read + 23.28 GB
-    # written in 49.81 ms (profiles/k_fused_clustered300m_dram.md)
-    ("b139f6fe313e84b4", "clustered-300000000"): 62.31e9,
+    # clustered-300M, one launch over its 54 batches: 39.07 GB read + 23.29 GB
+    # written in 49.63 ms (profiles/k_fused_clustered300m_dram.md)
+    ("b05ed5b4e3dd2b94", "clustered-300000000"): 62.36e9,
 }
 
 
