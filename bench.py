@@ -875,11 +875,12 @@ def serving_form(args, rank: int = 0) -> dict:
     # alternating, so that a box that drifts during the run (some get slower
     # over minutes) weighs on both alike; every server is built for its trace
     # and serves it once untimed first (the first run after a build is slower)
-    meas = {"serving": ([], [], [], [], [], []), "plain": ([], [], [], [], [], [])}
+    meas = {"serving": ([], [], [], [], [], [], [], []),
+            "plain": ([], [], [], [], [], [], [], [])}
     for t, tr in enumerate(traces):
         order = (("serving", False), ("plain", True))
         for name, plain in (order if t % 2 == 0 else order[::-1]):
-            lat, wait, reps, lwait, serv, slow = meas[name]
+            lat, wait, reps, lwait, serv, slow, slow_l, slow_r = meas[name]
             srv = serving.Server(specs, hbm_budget=budget, compute_slots=2, frame_ms=33.3,
                                  plain=plain)
             for warm in (True, False):
@@ -897,11 +898,13 @@ def serving_form(args, rank: int = 0) -> dict:
             serv += [(r.done - r.launched) * 1e3 for r in done]
             reps.append(srv.report())
             slow += [dict(x, trace=t) for x in reps[-1]["slowest"]]
+            slow_l += [dict(x, trace=t) for x in reps[-1]["slowest_launches"]]
+            slow_r += [dict(x, trace=t) for x in reps[-1]["slowest_renders"]]
             srv.close()
             del srv
             torch.cuda.empty_cache()
     for name in ("serving", "plain"):
-        lat, wait, reps, lwait, serv, slow = meas[name]
+        lat, wait, reps, lwait, serv, slow, slow_l, slow_r = meas[name]
         rep = dict(reps[0])
         # frames and scheduler figures are the first trace's; latencies,
         # waits and service times pool every timed trace's requests
@@ -910,6 +913,8 @@ def serving_form(args, rank: int = 0) -> dict:
         rep["service_ms"] = {"p50": float(np.percentile(serv, 50)),
                              "p99": float(np.percentile(serv, 99))}
         rep["slowest"] = sorted(slow, key=lambda x: -x["latency_ms"])[:8]
+        rep["slowest_launches"] = sorted(slow_l, key=lambda x: -x["device_ms"])[:6]
+        rep["slowest_renders"] = sorted(slow_r, key=lambda x: -x["device_ms"])[:4]
         rep["traces"] = len(traces)
         rep["requests"] = len(lat)
         rep["mpts_per_s"] = float(np.mean([x["mpts_per_s"] for x in reps]))

@@ -177,12 +177,15 @@ class Server:
         self.copy_stream = torch.cuda.Stream()
         self.pending = []      # arrived, not admitted (arrival order)
         self.queued = [[] for _ in self.trees]   # admitted, not launched, per octree
-        self.inflight = []     # (event, octree, requests, progress count before the launch)
+        self.inflight = []     # (event, octree, requests, progress count before the launch, record)
         self.busy = [False] * len(self.trees)
         self.finished = []
         self.frame_times = []
         self.frame_waits = []
         self.frame_spans = []  # (due, rendered) per frame, server clock
+        self.launch_log = []   # finished launches: octree, size, times, device events
+        self.render_log = []   # (octree, start event, end event) per render
+        self._frame_pending = False
         self.launches = 0
         self.early = 0         # requests completed before the end of their launch
         self.requeued = 0      # requests a launch's frame budget left for a later launch
@@ -202,6 +205,8 @@ class Server:
         self.pool = StagingPool(self.pool.size)
         self.finished, self.frame_times, self.frame_waits = [], [], []
         self.frame_spans = []
+        self.launch_log, self.render_log = [], []
+        self._frame_pending = False
         self.busy = [False] * len(self.trees)
         self.launches = 0
         self.early = 0         # requests completed before the end of their launch
@@ -224,9 +229,11 @@ class Server:
 
     def _poll(self):
         keep = []
-        for ev, k, reqs, base in self.inflight:
+        for ev, k, reqs, base, rec in self.inflight:
             if ev.query():
                 t = self.now()
+                rec["done"] = t
+                self.launch_log.append(rec)
                 applied = len(reqs)
                 if base is not None:
                     applied = min(applied, (self.trees[k].progress()[0] - base) & 0xFFFFFFFF)
@@ -251,7 +258,7 @@ class Server:
                         t = self.now() if t is None else t
                         self._complete(r, t)
                         self.early += 1
-            keep.append((ev, k, reqs, base))
+            keep.append((ev, k, reqs, base, rec))
         self.inflight = keep
 
     def _admit(self):
@@ -293,6 +300,10 @@ class Server:
                 r.launched = t
                 r.launch_points = lp
             base = None
+            # device time of the launch: from when its stream reaches it (its
+            # copies are done) to its end, whatever it waited for on the GPU
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev0.record(tree.stream)
             if self.plain:
                 rc = tree.insert(reqs[0].dev, stream=tree.stream, check=False)
             else:
@@ -307,9 +318,11 @@ class Server:
                                            budget_ns=budget)
             if rc != simlod.OK:
                 raise simlod.SimlodError(rc, "insert")
-            ev = torch.cuda.Event()
+            ev = torch.cuda.Event(enable_timing=True)
             ev.record(tree.stream)
-            self.inflight.append((ev, k, reqs, base))
+            rec = {"octree": k, "requests": len(reqs), "points": lp, "enqueued": t,
+                   "frame_pending": self._frame_pending, "ev0": ev0, "ev": ev}
+            self.inflight.append((ev, k, reqs, base, rec))
             self.busy[k] = True
             self.launches += 1
 
@@ -322,9 +335,12 @@ class Server:
             with torch.cuda.stream(tree.stream):
                 self.frames[k] = torch.empty((FRAME_H, FRAME_W), dtype=torch.int64,
                                              device="cuda")
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev0.record(tree.stream)
         tree.render(self.cams[k], self.frames[k])
-        ev = torch.cuda.Event()
+        ev = torch.cuda.Event(enable_timing=True)
         ev.record(tree.stream)
+        self.render_log.append((k, ev0, ev))
         return ev
 
     def render_frame(self):
@@ -393,6 +409,7 @@ class Server:
                     self.frame_waits.append(frame_t - due_t)
                     frame_due = due_t
                     due_t = None
+            self._frame_pending = due_t is not None or bool(frame_evs)
             if due_t is None and not frame_evs:
                 self._launch()
             elif self.frame_policy == "held":
@@ -441,6 +458,26 @@ class Server:
                          "launch_wait_ms": (r.launched - r.admitted) * 1e3,
                          "service_ms": (r.done - r.launched) * 1e3,
                          "launch_points": r.launch_points, "frame_pending_ms": pend * 1e3})
+        # the longest launches on the device (from when the stream reached
+        # them to their end) and the longest renders
+        launches = []
+        for rec in self.launch_log:
+            try:
+                dev = rec["ev0"].elapsed_time(rec["ev"])
+            except RuntimeError:
+                continue
+            launches.append({"octree": rec["octree"], "requests": rec["requests"],
+                             "points": rec["points"], "device_ms": dev,
+                             "host_ms": (rec["done"] - rec["enqueued"]) * 1e3,
+                             "frame_pending_at_start": rec["frame_pending"]})
+        launches.sort(key=lambda x: -x["device_ms"])
+        renders = []
+        for k, a, b in self.render_log:
+            try:
+                renders.append({"octree": k, "device_ms": a.elapsed_time(b)})
+            except RuntimeError:
+                continue
+        renders.sort(key=lambda x: -x["device_ms"])
         return {"requests": len(self.finished), "points": pts, "seconds": span,
                 "mpts_per_s": pts / span / 1e6 if span > 0 else 0.0,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)),
@@ -461,7 +498,8 @@ class Server:
                              "p99": float(np.percentile(ft, 99))},
                 "frame_wait_ms": {"p50": float(np.percentile(fw, 50)),
                                   "p99": float(np.percentile(fw, 99))},
-                "slowest": slow}
+                "slowest": slow, "slowest_launches": launches[:6],
+                "slowest_renders": renders[:4]}
 
     def close(self):
         for t in self.trees:

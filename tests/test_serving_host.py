@@ -101,6 +101,7 @@ def test_report_lists_the_slowest_requests_with_their_anatomy():
     srv.frame_spans = [(0.004, 0.007)]  # a frame pending from 4 to 7 ms
     srv.frame_times, srv.frame_waits, srv.gaps = [0.002], [0.001], [1e-4]
     srv.launches, srv.early, srv.requeued = 3, 0, 0
+    srv.launch_log, srv.render_log = [], []
     rep = srv.report()
     first, second = rep["slowest"][:2]
     assert first["octree"] == 1 and abs(first["latency_ms"] - 8.0) < 1e-9
@@ -109,6 +110,7 @@ def test_report_lists_the_slowest_requests_with_their_anatomy():
     assert abs(first["frame_pending_ms"] - 3.0) < 1e-9   # the whole frame lies inside it
     assert second["octree"] == 2 and abs(second["frame_pending_ms"] - 1.0) < 1e-9  # 4 to 5 ms
     assert rep["slowest"][2]["frame_pending_ms"] == 0.0
+    assert rep["slowest_launches"] == [] and rep["slowest_renders"] == []
 
 
 def test_unknown_frame_policy_is_refused():
