@@ -43,6 +43,11 @@ staging range is freed then too.
 Requests of one octree are applied in arrival order, which fixes their gidx:
 each octree ends up exactly as if its requests had been inserted alone, one
 after another (the tests compare both byte for byte).
+
+The report gives latency percentiles and the anatomy of the tail: the slowest
+requests (their admission wait, launch wait and service, and how long a frame
+was pending meanwhile), and the launches and renders that took longest on the
+device (CUDA events on the octree's stream around each of them).
 """
 from __future__ import annotations
 
